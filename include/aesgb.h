@@ -1,0 +1,158 @@
+/*
+ * aesgb.h -- C ABI of the GB300 (sm_103a) bulk AES library.
+ *
+ * The library implements the method of "GPU Accelerated AES Algorithm"
+ * (Wang & Chu, arXiv 1902.05234): AES in Electronic Codebook mode (section
+ * 3.1.1, eq (1): C_i = cipher(P_i), every 16-byte block independent), each
+ * round folded into four T-table lookups per column (section 3.2.3, eqs
+ * (22)-(26)).  Decryption, which the paper reports (Table 5) but does not
+ * describe, is the FIPS-197 5.3.5 equivalent inverse cipher with the
+ * analogous inverse tables.
+ *
+ * Conventions for every entry point:
+ *  - Return value: AES_OK (0) or a negative aes_status; aes_status_str()
+ *    names it.  No entry point aborts, traps or throws.
+ *  - "stream" is a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream.  GPU work is enqueued asynchronously on it; the call neither
+ *    allocates device memory nor synchronises (except where stated).  Errors
+ *    of the launch itself return AES_E_CUDA; faults during execution surface
+ *    at the caller's next synchronisation.
+ *  - Data pointers marked DEVICE must point to device memory of the current
+ *    device (cudaSetDevice) and stay valid until the enqueued work completes.
+ *    Pointers marked HOST are read during the call only.
+ *  - Blocks are whole 16-byte AES states; byte i of a block is state entry
+ *    s[i mod 4][i / 4] (FIPS-197 3.4).  There is no padding: callers pass a
+ *    block count.
+ *  - Round keys are the FIPS-197 expanded key as a byte string: word i of
+ *    rk holds bytes 4i..4i+3 of that string in memory order, so the layout is
+ *    the same on any host.
+ */
+#ifndef AESGB_H
+#define AESGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Status codes                                                              */
+/* ------------------------------------------------------------------------ */
+typedef enum aes_status {
+    AES_OK = 0,
+    AES_E_ARG = -1,      /* null pointer, size overflow or bad enum value      */
+    AES_E_KEYBITS = -2,  /* key size not 128, 192 or 256 bits                  */
+    AES_E_NROUNDS = -3,  /* nrounds not 10, 12 or 14                           */
+    AES_E_ALIGN = -4,    /* a block pointer not 16-byte aligned                */
+    AES_E_OVERLAP = -5,  /* in and out overlap without being equal             */
+    AES_E_CUDA = -6,     /* a CUDA runtime call failed (launch, attribute ...) */
+    AES_E_NOMEM = -7,    /* an allocation the call documents failed            */
+    AES_E_TIMEOUT = -8,  /* a bounded wait ran out                             */
+    AES_E_BUSY = -9,     /* admission refused: budget or slots full            */
+    AES_E_RANGE = -10,   /* a size above a documented maximum                  */
+    AES_E_NOTFOUND = -11,/* unknown key id or ticket                           */
+    AES_E_CONFIG = -12   /* launch configuration not supported                 */
+} aes_status;
+
+/* Name of a status code (static string; "unknown status" for other values). */
+const char *aes_status_str(int status);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int aes_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* Key schedule (host)                                                       */
+/* ------------------------------------------------------------------------ */
+
+/* Expand a cipher key into round keys.  Paper section 3.2.2 (key expansion
+ * and round-key selection, Nr+1 round keys of 128 bits) and Algorithm 1
+ * step 1; the steps (RotWord, SubWord, Rcon) follow FIPS-197 5.2.
+ *   keybits  128, 192 or 256; key: HOST, keybits/8 bytes.
+ *   rk_enc   HOST, caller-owned, at least 4*(Nr+1) words (60 always suffice):
+ *            the expanded key w[0 .. 4*Nr+3].  May be NULL.
+ *   rk_dec   HOST, same size: the equivalent-inverse-cipher schedule dw of
+ *            FIPS-197 5.3.5 (w with InvMixColumns applied to round keys
+ *            1..Nr-1), in the same word order as w.  May be NULL.
+ * Returns Nr (10, 12 or 14) on success, AES_E_KEYBITS or AES_E_ARG.
+ * Host only: touches no GPU. */
+int aes_expand_key(int keybits, const uint8_t *key, uint32_t *rk_enc, uint32_t *rk_dec);
+
+/* ------------------------------------------------------------------------ */
+/* Single-buffer ECB                                                         */
+/* ------------------------------------------------------------------------ */
+
+/* ECB encryption of nblocks independent 16-byte blocks, eq (1), each block
+ * run through the initial AddRoundKey, Nr-1 T-table rounds (eq (26)) and the
+ * final round without MixColumns (FIPS-197 5.1; Algorithm 1 as printed is
+ * wrong there).
+ *   rk       HOST, 4*(nrounds+1) words from aes_expand_key (rk_enc).  Copied
+ *            into the launch parameters: it may be freed on return.
+ *   nrounds  10, 12 or 14.
+ *   in, out  DEVICE, 16-byte aligned, nblocks*16 bytes each.  in == out
+ *            (in place) is allowed; any other overlap is AES_E_OVERLAP.
+ *   nblocks  0 is a no-op returning AES_OK.
+ * Launch configuration: the tuned configuration for (direction, nrounds,
+ * size) if one was recorded with aes_tune*, else the built-in default. */
+int aes_ecb_encrypt(const uint32_t *rk, int nrounds, const uint8_t *in, uint8_t *out,
+                    size_t nblocks, void *stream);
+
+/* ECB decryption, the same contract with rk_dec from aes_expand_key: the
+ * FIPS-197 5.3.5 equivalent inverse cipher (T-table form with the inverse
+ * tables, InvS in the final round). */
+int aes_ecb_decrypt(const uint32_t *rk_dec, int nrounds, const uint8_t *in, uint8_t *out,
+                    size_t nblocks, void *stream);
+
+/* Placement of the lookup tables (the paper's design axis of section 4.2). */
+typedef enum aes_layout {
+    AES_LAYOUT_R4 = 0,    /* 4 tables in shared memory, one copy per bank: 128 KiB
+                             (enc) / 160 KiB (dec); conflict-free, 1 CTA per SM   */
+    AES_LAYOUT_R1 = 1,    /* 1 table per bank-replicated + byte rotations: 64 KiB  */
+    AES_LAYOUT_P4 = 2,    /* 4 plain 1 KiB tables in shared memory (bank conflicts) */
+    AES_LAYOUT_CONST = 3  /* tables in constant memory, as in the paper (4.2)      */
+} aes_layout;
+
+/* A launch configuration of the ECB kernels. */
+typedef struct aes_launch_cfg {
+    int32_t threads;           /* threads per CTA, multiple of 32, 32..1024
+                                  (<= 512 when blocks_per_thread is 4)          */
+    int32_t blocks_per_thread; /* AES blocks per thread per pass: 1, 2 or 4
+                                  (granularity 16, 32 or 64 bytes per thread)   */
+    int32_t layout;            /* aes_layout                                     */
+    int32_t ctas_per_sm;       /* persistent grid = ctas_per_sm x SM count;
+                                  0 = as many as fit                             */
+} aes_launch_cfg;
+
+/* ECB with an explicit launch configuration (the autotuner and the
+ * placement study use it).  dir 0 = encrypt with rk_enc, 1 = decrypt with
+ * rk_dec; otherwise as aes_ecb_encrypt.  AES_E_CONFIG for an unsupported
+ * combination. */
+int aes_ecb_crypt_cfg(int dir, const uint32_t *rk, int nrounds, const uint8_t *in, uint8_t *out,
+                      size_t nblocks, const aes_launch_cfg *cfg, void *stream);
+
+/* The configuration aes_ecb_encrypt/decrypt would use for this call. */
+int aes_ecb_get_cfg(int dir, int nrounds, size_t nblocks, aes_launch_cfg *cfg);
+
+/* ------------------------------------------------------------------------ */
+/* Introspection                                                             */
+/* ------------------------------------------------------------------------ */
+
+/* Number of SMs of CUDA device `device` (>0), or AES_E_CUDA. */
+int aes_device_sm_count(int device);
+
+/* Copy one of the library's 256-entry tables (built at compile time) from
+ * HOST memory, no GPU needed:  which = 0 te0 (eq (22) column packed with row r
+ * in byte r), 1 td0 (inverse-cipher column 0e/09/0d/0b * InvS), 2 S-box,
+ * 3 inverse S-box (one byte per word).  out: HOST, 256 words. */
+int aes_host_table(int which, uint32_t *out);
+
+/* The same tables as the kernels see them in constant memory of the current
+ * device (synchronous copy).  out: HOST, 256 words. */
+int aes_device_table(int which, uint32_t *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AESGB_H */

@@ -1,0 +1,245 @@
+"""Thin ctypes binding of ``include/aesgb.h`` (same names, argument marshalling only).
+
+Every computation runs in ``libaesgb.so``'s CUDA kernels; this module only
+turns Python ints / numpy arrays / torch tensors into pointers and sizes and
+raises ``AesError`` on a negative status.  If the library has not been built,
+the first call raises: there is no CPU fallback.
+
+Pointer arguments accept an int (a raw address) or a torch tensor (its
+``data_ptr()``).  ``stream`` accepts None (torch's current CUDA stream), a
+``torch.cuda.Stream`` or a raw ``cudaStream_t`` int.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libaesgb.so")
+
+_lib = None
+_lock = threading.Lock()
+
+LAYOUT_R4, LAYOUT_R1, LAYOUT_P4, LAYOUT_CONST = 0, 1, 2, 3
+LAYOUT_NAMES = {0: "R4", 1: "R1", 2: "P4", 3: "CONST"}
+ENCRYPT, DECRYPT = 0, 1
+
+
+class AesError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {aes_status_str(status)} ({status})" if where else
+                         f"{aes_status_str(status)} ({status})")
+
+
+class aes_launch_cfg(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("blocks_per_thread", ctypes.c_int32),
+                ("layout", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+    def __repr__(self):
+        d = self.as_dict()
+        return (f"aes_launch_cfg(threads={d['threads']}, bpt={16 * d['blocks_per_thread']}B, "
+                f"layout={LAYOUT_NAMES.get(d['layout'], d['layout'])}, ctas_per_sm={d['ctas_per_sm']})")
+
+
+class aes_desc(ctypes.Structure):
+    _fields_ = [("rk", ctypes.c_uint64), ("in_", ctypes.c_uint64), ("out", ctypes.c_uint64),
+                ("nblocks", ctypes.c_uint64), ("nrounds", ctypes.c_int32), ("dir", ctypes.c_int32)]
+
+
+_vp = ctypes.c_void_p
+_sz = ctypes.c_size_t
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+_i = ctypes.c_int
+
+_SIGNATURES = {
+    "aes_status_str": (ctypes.c_char_p, [_i]),
+    "aes_version": (_i, []),
+    "aes_expand_key": (_i, [_i, _u8p, _u32p, _u32p]),
+    "aes_ecb_encrypt": (_i, [_u32p, _i, _vp, _vp, _sz, _vp]),
+    "aes_ecb_decrypt": (_i, [_u32p, _i, _vp, _vp, _sz, _vp]),
+    "aes_ecb_crypt_cfg": (_i, [_i, _u32p, _i, _vp, _vp, _sz, ctypes.POINTER(aes_launch_cfg), _vp]),
+    "aes_ecb_get_cfg": (_i, [_i, _i, _sz, ctypes.POINTER(aes_launch_cfg)]),
+    "aes_device_sm_count": (_i, [_i]),
+    "aes_host_table": (_i, [_i, _u32p]),
+    "aes_device_table": (_i, [_i, _u32p]),
+}
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded native library (loaded once; raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        with _lock:
+            if _lib is None:
+                if not os.path.exists(LIB_PATH):
+                    raise RuntimeError(
+                        f"{LIB_PATH} is missing: build it with `python -m paper_1902_05234_gb300.build` "
+                        "(there is no CPU fallback)")
+                h = ctypes.CDLL(LIB_PATH)
+                for name, (res, args) in _SIGNATURES.items():
+                    fn = getattr(h, name, None)
+                    if fn is None:
+                        continue
+                    fn.restype = res
+                    fn.argtypes = args
+                _lib = h
+    return _lib
+
+
+def declared_symbols() -> list[str]:
+    """Function names declared in include/aesgb.h (parsed from the header)."""
+    import re
+    hdr = os.path.join(os.path.dirname(_HERE), "include", "aesgb.h")
+    text = open(hdr).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(aes_[a-z0-9_]+)\s*\(", text)))
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        return int(x.ctypes.data)
+    raise TypeError(f"cannot take a pointer of {type(x)!r}")
+
+
+def _stream(s) -> int:
+    if s is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return int(torch.cuda.current_stream().cuda_stream)
+        except Exception:  # pragma: no cover - torch absent
+            pass
+        return 0
+    if isinstance(s, int):
+        return s
+    return int(s.cuda_stream)
+
+
+def _rk_arg(rk) -> ctypes.Array:
+    a = np.ascontiguousarray(np.asarray(rk, dtype=np.uint32))
+    return a.ctypes.data_as(_u32p), a
+
+
+def _check(st: int, where: str) -> int:
+    if st < 0:
+        raise AesError(st, where)
+    return st
+
+
+# ---------------------------------------------------------------------------
+# C ABI, same names
+# ---------------------------------------------------------------------------
+
+def aes_status_str(status: int) -> str:
+    return lib().aes_status_str(int(status)).decode()
+
+
+def aes_version() -> int:
+    return int(lib().aes_version())
+
+
+def aes_expand_key(keybits: int, key) -> tuple[np.ndarray, np.ndarray, int]:
+    """Returns (rk_enc, rk_dec, nrounds); rk_* are uint32[60] host arrays."""
+    k = np.ascontiguousarray(np.frombuffer(bytes(key), np.uint8) if isinstance(key, (bytes, bytearray))
+                             else np.asarray(key, np.uint8))
+    if k.size * 8 != keybits:
+        raise AesError(-1, f"aes_expand_key: key has {k.size} bytes for {keybits} bits")
+    enc = np.zeros(60, np.uint32)
+    dec = np.zeros(60, np.uint32)
+    nr = _check(lib().aes_expand_key(int(keybits), k.ctypes.data_as(_u8p),
+                                     enc.ctypes.data_as(_u32p), dec.ctypes.data_as(_u32p)),
+                "aes_expand_key")
+    return enc, dec, nr
+
+
+def aes_ecb_encrypt(rk, nrounds: int, in_, out, nblocks: int, stream=None) -> None:
+    p, _keep = _rk_arg(rk)
+    _check(lib().aes_ecb_encrypt(p, int(nrounds), _ptr(in_), _ptr(out), int(nblocks), _stream(stream)),
+           "aes_ecb_encrypt")
+
+
+def aes_ecb_decrypt(rk_dec, nrounds: int, in_, out, nblocks: int, stream=None) -> None:
+    p, _keep = _rk_arg(rk_dec)
+    _check(lib().aes_ecb_decrypt(p, int(nrounds), _ptr(in_), _ptr(out), int(nblocks), _stream(stream)),
+           "aes_ecb_decrypt")
+
+
+def make_cfg(threads=1024, blocks_per_thread=2, layout=LAYOUT_R4, ctas_per_sm=1) -> aes_launch_cfg:
+    return aes_launch_cfg(int(threads), int(blocks_per_thread), int(layout), int(ctas_per_sm))
+
+
+def aes_ecb_crypt_cfg(direction: int, rk, nrounds: int, in_, out, nblocks: int, cfg: aes_launch_cfg,
+                      stream=None) -> None:
+    p, _keep = _rk_arg(rk)
+    _check(lib().aes_ecb_crypt_cfg(int(direction), p, int(nrounds), _ptr(in_), _ptr(out), int(nblocks),
+                                   ctypes.byref(cfg), _stream(stream)), "aes_ecb_crypt_cfg")
+
+
+def aes_ecb_get_cfg(direction: int, nrounds: int, nblocks: int) -> aes_launch_cfg:
+    c = aes_launch_cfg()
+    _check(lib().aes_ecb_get_cfg(int(direction), int(nrounds), int(nblocks), ctypes.byref(c)),
+           "aes_ecb_get_cfg")
+    return c
+
+
+def aes_device_sm_count(device: int = 0) -> int:
+    return _check(lib().aes_device_sm_count(int(device)), "aes_device_sm_count")
+
+
+def aes_host_table(which: int) -> np.ndarray:
+    out = np.zeros(256, np.uint32)
+    _check(lib().aes_host_table(int(which), out.ctypes.data_as(_u32p)), "aes_host_table")
+    return out
+
+
+def aes_device_table(which: int) -> np.ndarray:
+    out = np.zeros(256, np.uint32)
+    _check(lib().aes_device_table(int(which), out.ctypes.data_as(_u32p)), "aes_device_table")
+    return out
+
+
+# ---------------------------------------------------------------------------
+# tensor conveniences (still one C call each)
+# ---------------------------------------------------------------------------
+
+def ecb_encrypt(key, data, out=None, stream=None):
+    """Encrypt a CUDA uint8 tensor (length a multiple of 16) with a raw key."""
+    return _ecb_tensor(ENCRYPT, key, data, out, stream)
+
+
+def ecb_decrypt(key, data, out=None, stream=None):
+    return _ecb_tensor(DECRYPT, key, data, out, stream)
+
+
+def _ecb_tensor(direction, key, data, out, stream):
+    import torch
+    kb = 8 * len(bytes(key)) if isinstance(key, (bytes, bytearray)) else 8 * int(np.asarray(key).size)
+    enc, dec, nr = aes_expand_key(kb, key)
+    if data.dtype != torch.uint8 or not data.is_cuda or data.numel() % 16:
+        raise AesError(-1, "ecb: need a CUDA uint8 tensor with a multiple of 16 bytes")
+    if out is None:
+        out = torch.empty_like(data)
+    n = data.numel() // 16
+    if direction == ENCRYPT:
+        aes_ecb_encrypt(enc, nr, data, out, n, stream)
+    else:
+        aes_ecb_decrypt(dec, nr, data, out, n, stream)
+    return out

@@ -1,0 +1,297 @@
+// aes_kernels.cuh -- sm_103a device code for bulk AES (T-table form).
+//
+// One AES block (16-byte state) is four 32-bit column words; byte r of a word
+// is row r.  A full round (Wang & Chu eq (26)) computes each output column as
+// four table lookups, one per row, XORed with the round-key column:
+//
+//   encrypt  e_j = T0[s_{0,j}] ^ T1[s_{1,j+1}] ^ T2[s_{2,j+2}] ^ T3[s_{3,j+3}] ^ k_j
+//   decrypt  e_j = D0[s_{0,j}] ^ D1[s_{1,j-1}] ^ D2[s_{2,j-2}] ^ D3[s_{3,j-3}] ^ k_j
+//
+// (column indices mod 4; T_k of eqs (22)-(25), D_k their inverse-cipher
+// analogues, FIPS-197 5.3.5).  The final round has no MixColumns: S-box bytes
+// (encrypt: byte 1 of T0, which is S(x); decrypt: an InvS table) are gathered
+// into the output column with byte permutes.
+//
+// The lookups are the bound (16 per block per round), so the tables sit in
+// shared memory laid out so that lane l of a warp only ever touches bank l:
+//
+//   R4  "replicated, four tables": entry x of table t for lane l at byte
+//       x*256 + 4*l + 128*(t&1) + 65536*(t>>1).  The address is ONE byte
+//       permute of the state word with a per-lane constant (x lands in bits
+//       8..15, 4*l in bits 0..7) plus an immediate.  128 KiB; decryption adds
+//       InvS at 131072 + x*128 + 4*l (160 KiB).
+//   R1  one table per bank-replicated at x*256 + 4*l, the other three by
+//       byte rotation (one funnel shift each); decryption keeps InvS in the
+//       gaps at +128.  64 KiB.
+//   P4  four plain 1 KiB tables (t*1024 + 4x): the paper's "shared memory"
+//       alternative of section 4.2, with bank conflicts.
+//   CONST  the tables in constant memory, as the paper places them (4.2).
+//
+// Round keys are uniform across the grid (section 4.3 puts them in constant
+// memory): the single-buffer kernels take them as kernel parameters, so each
+// XOR with a key word reads the constant bank directly.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "aes_tables.h"
+
+namespace aesgb {
+
+enum : int { kLayoutR4 = 0, kLayoutR1 = 1, kLayoutP4 = 2, kLayoutConst = 3 };
+enum : int { kEncrypt = 0, kDecrypt = 1 };
+
+constexpr int kMaxRkWords = 60;  // 4 * (14 + 1)
+
+// Round keys in the order they are applied: words 4i..4i+3 are the key of
+// step i = 0..Nr (for decryption the host reverses the dw schedule).
+struct RoundKeys {
+    uint32_t w[kMaxRkWords];
+};
+
+struct EcbArgs {
+    const uint4 *in;
+    uint4 *out;
+    unsigned long long nblocks;
+    RoundKeys rk;
+};
+
+__host__ __device__ constexpr uint32_t table_smem_bytes(int dir, int layout) {
+    return layout == kLayoutR4   ? (dir == kDecrypt ? 160u * 1024u : 128u * 1024u)
+           : layout == kLayoutR1 ? 64u * 1024u
+           : layout == kLayoutP4 ? (dir == kDecrypt ? 5u * 1024u : 4u * 1024u)
+                                 : 0u;
+}
+
+constexpr int max_threads_for_nb(int nb) { return nb >= 4 ? 512 : 1024; }
+
+// Each module keeps its own copy of the compile-time tables in constant memory.
+static __constant__ ConstTables c_tab = make_const_tables();
+
+__device__ __forceinline__ uint32_t lds32(const uint8_t *smem, uint32_t off) {
+    return *reinterpret_cast<const uint32_t *>(smem + off);
+}
+__device__ __forceinline__ void sts32(uint8_t *smem, uint32_t off, uint32_t v) {
+    *reinterpret_cast<uint32_t *>(smem + off) = v;
+}
+__device__ __forceinline__ uint32_t rotl32(uint32_t v, int n) {
+    return n == 0 ? v : __funnelshift_l(v, v, n);
+}
+// Byte b of s moved to bits 8..15, byte 0 of `low` kept in bits 0..7, upper
+// half from `low` too (zero): x*256 + lane*4 in one PRMT.
+__device__ __forceinline__ uint32_t byte_to_bits8(uint32_t s, uint32_t low, int b) {
+    return __byte_perm(s, low, 0x7604u | (static_cast<uint32_t>(b) << 4));
+}
+// Byte b of s as an integer 0..255.
+__device__ __forceinline__ uint32_t byte_of(uint32_t s, int b) {
+    return __byte_perm(s, 0u, 0x4440u | static_cast<uint32_t>(b));
+}
+
+// ---------------------------------------------------------------------------
+// Table policies.  lookup(t, s, b): table t at index byte b of word s.
+// final_word(s, b): a word whose byte kFinalByte is S(x) (encrypt) or IS(x)
+// (decrypt) for x = byte b of s.
+// ---------------------------------------------------------------------------
+template <int LAYOUT, int DIR> struct Tab;
+
+template <int DIR> struct Tab<kLayoutR4, DIR> {
+    static constexpr int kFinalByte = DIR == kEncrypt ? 1 : 0;
+    const uint8_t *smem;
+    uint32_t lane4, lane8;
+    __device__ Tab(const uint8_t *s, uint32_t lane) : smem(s), lane4(lane * 4u), lane8(lane * 8u) {}
+    __device__ static void fill(uint8_t *smem, int tid, int nthr) {
+        for (int i = tid; i < 256 * 32; i += nthr) {
+            const int x = i >> 5, l = i & 31;
+            const uint32_t o = static_cast<uint32_t>(x * 256 + l * 4);
+            const uint32_t(*t)[256] = DIR == kEncrypt ? c_tab.te : c_tab.td;
+            sts32(smem, o, t[0][x]);
+            sts32(smem, o + 128u, t[1][x]);
+            sts32(smem, o + 65536u, t[2][x]);
+            sts32(smem, o + 65536u + 128u, t[3][x]);
+            if (DIR == kDecrypt)
+                sts32(smem, 131072u + static_cast<uint32_t>(x * 128 + l * 4), c_tab.is[x]);
+        }
+    }
+    __device__ __forceinline__ uint32_t lookup(int t, uint32_t s, int b) const {
+        return lds32(smem, byte_to_bits8(s, lane4, b) + 128u * (t & 1) + 65536u * (t >> 1));
+    }
+    __device__ __forceinline__ uint32_t final_word(uint32_t s, int b) const {
+        if (DIR == kEncrypt) return lds32(smem, byte_to_bits8(s, lane4, b));
+        return lds32(smem, 131072u + (byte_to_bits8(s, lane8, b) >> 1));
+    }
+};
+
+template <int DIR> struct Tab<kLayoutR1, DIR> {
+    static constexpr int kFinalByte = DIR == kEncrypt ? 1 : 0;
+    const uint8_t *smem;
+    uint32_t lane4;
+    __device__ Tab(const uint8_t *s, uint32_t lane) : smem(s), lane4(lane * 4u) {}
+    __device__ static void fill(uint8_t *smem, int tid, int nthr) {
+        for (int i = tid; i < 256 * 32; i += nthr) {
+            const int x = i >> 5, l = i & 31;
+            const uint32_t o = static_cast<uint32_t>(x * 256 + l * 4);
+            sts32(smem, o, DIR == kEncrypt ? c_tab.te[0][x] : c_tab.td[0][x]);
+            if (DIR == kDecrypt) sts32(smem, o + 128u, c_tab.is[x]);
+        }
+    }
+    __device__ __forceinline__ uint32_t lookup(int t, uint32_t s, int b) const {
+        return rotl32(lds32(smem, byte_to_bits8(s, lane4, b)), 8 * t);
+    }
+    __device__ __forceinline__ uint32_t final_word(uint32_t s, int b) const {
+        return lds32(smem, byte_to_bits8(s, lane4, b) + (DIR == kEncrypt ? 0u : 128u));
+    }
+};
+
+template <int DIR> struct Tab<kLayoutP4, DIR> {
+    static constexpr int kFinalByte = DIR == kEncrypt ? 1 : 0;
+    const uint8_t *smem;
+    __device__ Tab(const uint8_t *s, uint32_t) : smem(s) {}
+    __device__ static void fill(uint8_t *smem, int tid, int nthr) {
+        const int n = DIR == kEncrypt ? 1024 : 1280;
+        for (int i = tid; i < n; i += nthr) {
+            uint32_t v;
+            if (i < 1024) v = DIR == kEncrypt ? c_tab.te[i >> 8][i & 255] : c_tab.td[i >> 8][i & 255];
+            else v = c_tab.is[i - 1024];
+            sts32(smem, static_cast<uint32_t>(i * 4), v);
+        }
+    }
+    __device__ __forceinline__ uint32_t lookup(int t, uint32_t s, int b) const {
+        return lds32(smem, (byte_of(s, b) << 2) + 1024u * t);
+    }
+    __device__ __forceinline__ uint32_t final_word(uint32_t s, int b) const {
+        return lds32(smem, (byte_of(s, b) << 2) + (DIR == kEncrypt ? 0u : 4096u));
+    }
+};
+
+template <int DIR> struct Tab<kLayoutConst, DIR> {
+    static constexpr int kFinalByte = DIR == kEncrypt ? 1 : 0;
+    __device__ Tab(const uint8_t *, uint32_t) {}
+    __device__ static void fill(uint8_t *, int, int) {}
+    __device__ __forceinline__ uint32_t lookup(int t, uint32_t s, int b) const {
+        return DIR == kEncrypt ? c_tab.te[t][byte_of(s, b)] : c_tab.td[t][byte_of(s, b)];
+    }
+    __device__ __forceinline__ uint32_t final_word(uint32_t s, int b) const {
+        return DIR == kEncrypt ? c_tab.te[0][byte_of(s, b)] : c_tab.is[byte_of(s, b)];
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Rounds
+// ---------------------------------------------------------------------------
+
+// Column of the input state whose row-r byte feeds output column j.
+template <int DIR> __device__ constexpr int src_col(int j, int r) {
+    return DIR == kEncrypt ? ((j + r) & 3) : ((j - r + 4) & 3);
+}
+
+// eq (26): one full round (SubBytes, ShiftRows, MixColumns, AddRoundKey or the
+// inverse-cipher equivalents) on one state.
+template <int DIR, class TabT, class Key>
+__device__ __forceinline__ void full_round(const TabT &tab, uint32_t (&s)[4], const Key &k, int kw) {
+    uint32_t t[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        uint32_t v = tab.lookup(0, s[src_col<DIR>(j, 0)], 0) ^ tab.lookup(1, s[src_col<DIR>(j, 1)], 1);
+        v ^= tab.lookup(2, s[src_col<DIR>(j, 2)], 2) ^ tab.lookup(3, s[src_col<DIR>(j, 3)], 3);
+        t[j] = v ^ k(kw + j);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s[j] = t[j];
+}
+
+// Final round: (Inv)SubBytes + (Inv)ShiftRows + AddRoundKey, no MixColumns.
+template <int DIR, class TabT, class Key>
+__device__ __forceinline__ void final_round(const TabT &tab, uint32_t (&s)[4], const Key &k, int kw) {
+    constexpr uint32_t fb = TabT::kFinalByte;
+    constexpr uint32_t sel_lo = ((4u + fb) << 4) | fb;           // bytes 0,1 <- w0.fb, w1.fb
+    constexpr uint32_t sel_hi = ((4u + fb) << 12) | (fb << 8);   // bytes 2,3 <- w2.fb, w3.fb
+    uint32_t t[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t w0 = tab.final_word(s[src_col<DIR>(j, 0)], 0);
+        const uint32_t w1 = tab.final_word(s[src_col<DIR>(j, 1)], 1);
+        const uint32_t w2 = tab.final_word(s[src_col<DIR>(j, 2)], 2);
+        const uint32_t w3 = tab.final_word(s[src_col<DIR>(j, 3)], 3);
+        const uint32_t lo = __byte_perm(w0, w1, sel_lo);
+        const uint32_t hi = __byte_perm(w2, w3, sel_hi);
+        t[j] = __byte_perm(lo, hi, 0x7610u) ^ k(kw + j);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s[j] = t[j];
+}
+
+// Key accessor over the kernel-parameter round keys (constant bank).
+struct ParamKey {
+    const uint32_t *w;
+    __device__ __forceinline__ uint32_t operator()(int i) const { return w[i]; }
+};
+
+// Full cipher (encrypt) or equivalent inverse cipher (decrypt) on NB states.
+template <int DIR, int NR, int NB, class TabT, class Key>
+__device__ __forceinline__ void cipher_states(const TabT &tab, const Key &k, uint32_t (&s)[NB][4]) {
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) s[i][j] ^= k(j);
+#pragma unroll
+    for (int r = 1; r < NR; ++r)
+#pragma unroll
+        for (int i = 0; i < NB; ++i) full_round<DIR>(tab, s[i], k, 4 * r);
+#pragma unroll
+    for (int i = 0; i < NB; ++i) final_round<DIR>(tab, s[i], k, 4 * NR);
+}
+
+__device__ __forceinline__ uint4 ld_block(const uint4 *p) { return __ldcs(p); }
+__device__ __forceinline__ void st_block(uint4 *p, uint4 v) { __stcs(p, v); }
+
+// ---------------------------------------------------------------------------
+// Single-buffer ECB kernel (persistent, grid-stride).  Warp w of the grid owns
+// blocks [base, base + 32*NB) of each pass, lane l blocks base + l + 32*i, so
+// every warp-wide 128-bit load/store covers 512 contiguous bytes.  The next
+// pass's blocks are loaded before the current ones are ciphered.
+// ---------------------------------------------------------------------------
+template <int DIR, int NR, int NB, int LAYOUT>
+__global__ void __launch_bounds__(max_threads_for_nb(NB), 1)
+    ecb_kernel(const __grid_constant__ EcbArgs a) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    Tab<LAYOUT, DIR>::fill(smem, threadIdx.x, blockDim.x);
+    __syncthreads();
+
+    const uint32_t lane = threadIdx.x & 31u;
+    const Tab<LAYOUT, DIR> tab(smem, lane);
+    const ParamKey key{a.rk.w};
+    const unsigned long long n = a.nblocks;
+    const unsigned long long wpc = blockDim.x >> 5;
+    const unsigned long long step = static_cast<unsigned long long>(gridDim.x) * wpc * 32ull * NB;
+    unsigned long long base = (blockIdx.x * wpc + (threadIdx.x >> 5)) * 32ull * NB;
+
+    uint4 cur[NB];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        const unsigned long long b = base + lane + 32ull * i;
+        cur[i] = b < n ? ld_block(a.in + b) : make_uint4(0, 0, 0, 0);
+    }
+    for (; base < n; base += step) {
+        uint4 nxt[NB];
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            const unsigned long long b = base + step + lane + 32ull * i;
+            nxt[i] = b < n ? ld_block(a.in + b) : make_uint4(0, 0, 0, 0);
+        }
+        uint32_t s[NB][4];
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            s[i][0] = cur[i].x; s[i][1] = cur[i].y; s[i][2] = cur[i].z; s[i][3] = cur[i].w;
+        }
+        cipher_states<DIR, NR, NB>(tab, key, s);
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            const unsigned long long b = base + lane + 32ull * i;
+            if (b < n) st_block(a.out + b, make_uint4(s[i][0], s[i][1], s[i][2], s[i][3]));
+            cur[i] = nxt[i];
+        }
+    }
+}
+
+}  // namespace aesgb

@@ -1,0 +1,31 @@
+// capi_internal.h -- host helpers shared by the C-ABI translation units.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include "aesgb.h"
+
+namespace aesgb {
+
+struct RoundKeys;
+
+int current_device(int *dev);
+int sm_count(int dev);
+int ensure_smem_attr(const void *fn, int dev, uint32_t bytes);
+int check_nrounds(int nr);
+int check_buffers(const void *in, const void *out, size_t nblocks);
+void order_round_keys(int dir, const uint32_t *rk, int nr, RoundKeys *out);
+int validate_cfg(const aes_launch_cfg &c);
+int persistent_grid(const void *fn, int dev, const aes_launch_cfg &c, uint32_t smem,
+                    unsigned long long work_items_per_cta, unsigned long long total_items, int *grid);
+int launch_ecb(int dir, const uint32_t *rk, int nr, const uint8_t *in, uint8_t *out, size_t nblocks,
+               const aes_launch_cfg &c, void *stream);
+
+// keysched.cpp
+int expand_key_host(int keybits, const uint8_t *key, uint32_t *rk_enc, uint32_t *rk_dec);
+
+// tune.cpp
+aes_launch_cfg default_cfg(int dir, int nrounds, size_t nblocks);
+aes_launch_cfg tuned_or_default_cfg(int dir, int nrounds, size_t nblocks);
+
+}  // namespace aesgb

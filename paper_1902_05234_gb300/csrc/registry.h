@@ -1,0 +1,17 @@
+// registry.h -- host-side lookup of the kernel instantiations compiled in the
+// per-direction translation units (ecb_enc.cu, ecb_dec.cu).
+#pragma once
+#include <cstdint>
+
+namespace aesgb {
+
+// Host stub of ecb_kernel<dir, nr, nb, layout>, or nullptr if that
+// combination is not compiled.
+const void *ecb_kernel_enc(int nr, int nb, int layout);
+const void *ecb_kernel_dec(int nr, int nb, int layout);
+
+// Copy table `which` (0 te0, 1 td0, 2 S-box, 3 InvS) from the constant bank of
+// the encrypt module on the current device.  Returns a cudaError_t value.
+int ecb_module_const_table(int which, uint32_t *out);
+
+}  // namespace aesgb

@@ -1,0 +1,93 @@
+"""Host-side tests of the C-ABI library (no GPU): it loads, exports every
+symbol include/aesgb.h declares, and its host logic (key schedule, tables,
+argument checks that run before any CUDA call) agrees with the oracle."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1902_05234_gb300 import aesgb
+from paper_1902_05234_gb300 import workloads as wl
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return aesgb.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = aesgb.declared_symbols()
+    assert "aes_ecb_encrypt" in names and "aes_expand_key" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings(lib):
+    for st in range(0, -13, -1):
+        s = aesgb.aes_status_str(st)
+        assert s and s != "unknown status"
+    assert aesgb.aes_status_str(5) == "unknown status"
+
+
+@pytest.mark.parametrize("keybits", [128, 192, 256])
+def test_expand_key_matches_oracle(orc, keybits):
+    for seed in range(25):
+        key = wl.random_key(keybits, seed)
+        enc, dec, nr = aesgb.aes_expand_key(keybits, key)
+        w, onr = orc.key_expansion(key)
+        assert nr == onr
+        nw = 4 * (nr + 1)
+        assert enc[:nw].view(np.uint8).tobytes() == w.tobytes()
+        dw = orc.eq_inv_schedule(w, nr)
+        assert dec[:nw].view(np.uint8).tobytes() == dw.tobytes()
+
+
+def test_expand_key_errors(lib):
+    key = (ctypes.c_uint8 * 32)()
+    for bits in (0, 64, 127, 129, 512, -128):
+        assert lib.aes_expand_key(bits, key, None, None) == -2
+    assert lib.aes_expand_key(128, None, None, None) == -1
+
+
+def test_host_tables_match_oracle(orc):
+    te0, td0 = aesgb.aes_host_table(0), aesgb.aes_host_table(1)
+    sb, isb = aesgb.aes_host_table(2), aesgb.aes_host_table(3)
+    assert np.array_equal(sb, orc.sbox_table().astype(np.uint32))
+    assert np.array_equal(isb, orc.inv_sbox_table().astype(np.uint32))
+    for x in range(256):
+        # eq (22): T0 column, row r in byte r
+        col = orc.ttable(0, x)
+        assert int(te0[x]) == int.from_bytes(bytes(col.tolist()), "little")
+        # inverse-cipher column: (0e, 09, 0d, 0b) * InvS(x)
+        i = orc.inv_sbox(x)
+        exp = bytes([orc.gf_mul(0x0E, i), orc.gf_mul(0x09, i), orc.gf_mul(0x0D, i), orc.gf_mul(0x0B, i)])
+        assert int(td0[x]) == int.from_bytes(exp, "little")
+
+
+def test_argument_checks_before_cuda(lib):
+    rk = (ctypes.c_uint32 * 60)()
+    A = 1 << 20  # fake, never dereferenced: every call below fails validation first
+    assert lib.aes_ecb_encrypt(rk, 11, A, A + 4096, 4, None) == -3      # nrounds
+    assert lib.aes_ecb_decrypt(rk, 9, A, A + 4096, 4, None) == -3
+    assert lib.aes_ecb_encrypt(None, 10, A, A + 4096, 4, None) == -1    # null rk
+    assert lib.aes_ecb_encrypt(rk, 10, A, A + 4096, 0, None) == 0       # empty: no-op
+    assert lib.aes_ecb_encrypt(rk, 10, 0, A, 4, None) == -1             # null in
+    assert lib.aes_ecb_encrypt(rk, 10, A + 8, A + 4096, 4, None) == -4  # misaligned
+    assert lib.aes_ecb_encrypt(rk, 10, A, A + 4104, 4, None) == -4
+    assert lib.aes_ecb_encrypt(rk, 10, A, A + 16, 4, None) == -5        # partial overlap
+    assert lib.aes_ecb_encrypt(rk, 10, A + 48, A, 4, None) == -5
+    assert lib.aes_ecb_encrypt(rk, 10, A, A + 4096, 1 << 61, None) == -1  # nblocks*16 overflows
+    bad = aesgb.make_cfg(threads=1000)
+    assert lib.aes_ecb_crypt_cfg(0, rk, 10, A, A + 4096, 4, ctypes.byref(bad), None) == -12
+    bad = aesgb.make_cfg(threads=1024, blocks_per_thread=4)
+    assert lib.aes_ecb_crypt_cfg(0, rk, 10, A, A + 4096, 4, ctypes.byref(bad), None) == -12
+    bad = aesgb.make_cfg(blocks_per_thread=3)
+    assert lib.aes_ecb_crypt_cfg(1, rk, 10, A, A + 4096, 4, ctypes.byref(bad), None) == -12
+    assert lib.aes_ecb_crypt_cfg(2, rk, 10, A, A + 4096, 4, ctypes.byref(aesgb.make_cfg()), None) == -1
+
+
+def test_default_cfg_is_valid():
+    for d in (0, 1):
+        for nr in (10, 12, 14):
+            c = aesgb.aes_ecb_get_cfg(d, nr, 1 << 20)
+            assert c.threads % 32 == 0 and c.blocks_per_thread in (1, 2, 4)

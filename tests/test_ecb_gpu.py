@@ -1,0 +1,138 @@
+"""ECB parity on the GPU: every key size, both directions, every launch
+configuration the tuner can pick, edge sizes, in place, guard bytes.
+Bit-exact against the CPU oracle (integer work: tolerance 0)."""
+import numpy as np
+import pytest
+
+from paper_1902_05234_gb300 import aesgb
+from paper_1902_05234_gb300 import workloads as wl
+from gpu_util import gpu_ecb, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+KEYBITS = [128, 192, 256]
+
+
+def oracle_ecb(orc, direction, key, data):
+    return orc.ecb(direction, key, data, nthreads=8)
+
+
+def test_c1_1mib_encrypt_then_decrypt(orc):
+    """1 MiB (65,536 blocks) of seeded random bytes, one 128-bit key: encrypt,
+    then decrypt the ciphertext; both compared in full with the oracle."""
+    data = wl.random_bytes(1 << 20, 1)
+    key = wl.random_key(128, 1).tobytes()
+    ct, ok = gpu_ecb(0, key, data, guard=4096)
+    assert ok
+    assert np.array_equal(ct, oracle_ecb(orc, 0, key, data))
+    pt, ok = gpu_ecb(1, key, ct, guard=4096)
+    assert ok
+    assert np.array_equal(pt, data)
+    assert np.array_equal(pt, oracle_ecb(orc, 1, key, ct))
+
+
+SIZES = [1, 2, 3, 31, 32, 33, 63, 64, 65, 1023, 1024, 1025, 2047, 2048, 2049, 4097, 65537, 311297]
+
+
+@pytest.mark.parametrize("keybits", KEYBITS)
+@pytest.mark.parametrize("direction", [0, 1])
+def test_edge_sizes_default_cfg(orc, keybits, direction):
+    key = wl.random_key(keybits, 2).tobytes()
+    for n in SIZES:
+        data = wl.random_bytes(16 * n, 100 + n)
+        got, ok = gpu_ecb(direction, key, data, guard=256)
+        assert ok, f"guard bytes touched at n={n}"
+        assert np.array_equal(got, oracle_ecb(orc, direction, key, data)), f"n={n}"
+
+
+def all_cfgs():
+    out = []
+    for layout in (aesgb.LAYOUT_R4, aesgb.LAYOUT_R1, aesgb.LAYOUT_P4, aesgb.LAYOUT_CONST):
+        nbs = (1, 2, 4) if layout in (aesgb.LAYOUT_R4, aesgb.LAYOUT_R1) else (1,)
+        for nb in nbs:
+            for threads in (64, 256, 512, 1024):
+                if nb == 4 and threads > 512:
+                    continue
+                for cps in (0, 1):
+                    out.append(aesgb.make_cfg(threads, nb, layout, cps))
+    return out
+
+
+@pytest.mark.parametrize("keybits", KEYBITS)
+@pytest.mark.parametrize("direction", [0, 1])
+def test_every_cfg(orc, keybits, direction):
+    """Each configuration at a ragged size that spans several grid passes for
+    the small configurations and a partial pass for the large ones."""
+    n = 400_003
+    key = wl.random_key(keybits, 3).tobytes()
+    data = wl.random_bytes(16 * n, 7)
+    exp = oracle_ecb(orc, direction, key, data)
+    for cfg in all_cfgs():
+        got, ok = gpu_ecb(direction, key, data, cfg=cfg, guard=64)
+        assert ok, repr(cfg)
+        assert np.array_equal(got, exp), repr(cfg)
+
+
+@pytest.mark.parametrize("keybits", KEYBITS)
+def test_in_place(orc, keybits):
+    key = wl.random_key(keybits, 4).tobytes()
+    data = wl.random_bytes(16 * 100_001, 8)
+    ct, ok = gpu_ecb(0, key, data, inplace=True, guard=512)
+    assert ok and np.array_equal(ct, oracle_ecb(orc, 0, key, data))
+    pt, ok = gpu_ecb(1, key, ct, inplace=True, guard=512)
+    assert ok and np.array_equal(pt, data)
+
+
+def test_16_byte_offsets_and_zero_blocks(orc):
+    torch = torch_cuda()
+    key = wl.random_key(128, 5).tobytes()
+    enc, dec, nr = aesgb.aes_expand_key(128, key)
+    data = wl.random_bytes(16 * 1000, 9)
+    src = torch.from_numpy(data).cuda()
+    dst = torch.zeros(16 * 1002, dtype=torch.uint8, device="cuda")
+    # in at +16 bytes, out at +32 bytes: both only 16-byte aligned
+    aesgb.aes_ecb_encrypt(enc, nr, src.data_ptr() + 16, dst.data_ptr() + 32, 999)
+    torch.cuda.synchronize()
+    got = dst.cpu().numpy()
+    assert np.array_equal(got[32:32 + 16 * 999], oracle_ecb(orc, 0, key, data[16:]))
+    assert not got[:32].any() and not got[32 + 16 * 999:].any()
+    before = dst.clone()
+    aesgb.aes_ecb_encrypt(enc, nr, src.data_ptr(), dst.data_ptr(), 0)   # no-op
+    torch.cuda.synchronize()
+    assert torch.equal(before, dst)
+    with pytest.raises(aesgb.AesError) as e:
+        aesgb.aes_ecb_encrypt(enc, nr, src.data_ptr() + 8, dst.data_ptr(), 10)
+    assert e.value.status == -4
+
+
+def test_ecb_invariants_on_device():
+    """Equal blocks -> equal ciphertext; permuted input -> permuted output."""
+    torch = torch_cuda()
+    key = wl.random_key(256, 6).tobytes()
+    g = np.random.default_rng(11)
+    blocks = g.integers(0, 256, (50_000, 16), dtype=np.uint8)
+    blocks[1000:2000] = blocks[5]
+    ct, _ = gpu_ecb(0, key, blocks.reshape(-1))
+    ct = ct.reshape(-1, 16)
+    assert (ct[1000:2000] == ct[5]).all()
+    perm = g.permutation(blocks.shape[0])
+    ctp, _ = gpu_ecb(0, key, blocks[perm].reshape(-1))
+    assert np.array_equal(ctp.reshape(-1, 16), ct[perm])
+
+
+def test_device_tables_match_host_tables():
+    torch_cuda()
+    for which in range(4):
+        assert np.array_equal(aesgb.aes_device_table(which), aesgb.aes_host_table(which))
+
+
+def test_tensor_convenience_roundtrip(orc):
+    torch = torch_cuda()
+    key = wl.random_key(192, 7).tobytes()
+    data = wl.random_bytes(16 * 4096, 12)
+    x = torch.from_numpy(data).cuda()
+    c = aesgb.ecb_encrypt(key, x)
+    p = aesgb.ecb_decrypt(key, c)
+    torch.cuda.synchronize()
+    assert np.array_equal(c.cpu().numpy(), oracle_ecb(orc, 0, key, data))
+    assert torch.equal(p, x)
