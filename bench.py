@@ -1,0 +1,489 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 bulk AES library (one JSON line on rank 0).
+
+Workload of a step (per rank, weak scaling): AES-128 ECB over a 1 GiB buffer of
+seeded uniform random bytes already resident in HBM -- the host key schedule
+(aes_expand_key), encryption of the buffer into a second buffer, decryption of
+that ciphertext into a third -- i.e. every step of the single-buffer hot path in
+both directions.  `value` is Gbit/s of plaintext+ciphertext processed (2 GiB per
+rank per step), device-timed with CUDA events on the launching stream, the max
+over ranks.  Inputs (1 GiB) are larger than the 129 MB L2, so no flush is needed.
+
+Additional objects on the same line:
+  roofline     the encryption kernel against its bound, the shared-memory lookup
+               rate (16 lookups of 4 B per block per round; 32 lanes x 4 B per clock
+               per SM), at the SM clock sampled during the timed region.
+  e2e          the same two passes through aes_ecb_host: page-locked host buffers,
+               host->device and device->host copies inside the timed region.
+  cpu_baseline the CPU oracle timed on this host's cores on a bounded sample.
+  sweep        single-buffer Gbit/s over 1 MiB..4 GiB x AES-128/192/256 x enc/dec.
+  clocks       nvidia-smi SM clock and throttle reasons sampled while timing.
+
+`--impl reference` times the CPU oracle instead (the reference arm of this
+method is the plain FIPS-197 CPU implementation), on a bounded sample per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+GIB = 1 << 30
+MIB = 1 << 20
+METRIC = "AES-128 ECB enc/dec throughput (single 1 GiB buffer, HBM-resident)"
+UNIT = "Gbit/s"
+KERNEL_SOURCES = ["paper_1902_05234_gb300/csrc/aes_kernels.cuh",
+                  "paper_1902_05234_gb300/csrc/aes_tables.h"]
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    p.add_argument("--bytes", type=int, default=GIB, help="buffer size per rank")
+    p.add_argument("--keybits", type=int, default=128)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-sweep", action="store_true")
+    return p.parse_args()
+
+
+def workload_config(args, world):
+    return {
+        "workload": f"AES-{args.keybits} ECB encrypt then decrypt of one {args.bytes // MIB} MiB buffer "
+                    f"({args.bytes // 16:,} blocks) per GPU, uniform random bytes, one random key",
+        "key_bits": args.keybits,
+        "buffer_bytes": args.bytes,
+        "mode": "ECB",
+        "l2": "inputs larger than L2 (buffer > 129 MB), no flush",
+        "parallelism": f"independent shards x{world}" if world > 1 else "single GPU",
+    }
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (timing barrier and max over ranks only)
+# ---------------------------------------------------------------------------
+
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+    REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines: list[str] = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={','.join(self.FIELDS)}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.dev)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+        time.sleep(0.25)  # first sample before the timed work starts
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self._t:
+                self._t.join(timeout=5)
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(self.REASONS, parts[3:]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline inputs
+# ---------------------------------------------------------------------------
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, keybits: int, nbytes: int):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    want = kernel_source_hash()
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        kv = dict(tok.split("=", 1) for tok in line.split() if "=" in tok)
+        if (kv.get("kernel") == kernel and kv.get("src") == want and int(kv.get("keybits", 0)) == keybits
+                and int(kv.get("buffer_bytes", 0)) == nbytes):
+            return int(kv["dram_bytes_per_launch"])
+    return None
+
+
+def nrounds_of(keybits: int) -> int:
+    return {128: 10, 192: 12, 256: 14}[keybits]
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
+
+def oracle_rate(o, nthreads: int) -> float:
+    """Bytes/s of the oracle (encrypt) on this host, from a short probe."""
+    from paper_1902_05234_gb300 import workloads as wl
+    data = wl.random_bytes(256 * 1024, 90)
+    key = wl.random_key(128, 90).tobytes()
+    t = time.perf_counter()
+    o.ecb(0, key, data, nthreads=nthreads)
+    return data.size / max(time.perf_counter() - t, 1e-6)
+
+
+def cpu_baseline(keybits: int, seconds: float = 10.0) -> dict:
+    """The oracle as it stands, encrypt + decrypt of a seeded sample sized to
+    take about `seconds` on all host cores."""
+    import oracle
+    from paper_1902_05234_gb300 import workloads as wl
+    o = oracle.Oracle()
+    cores = os.cpu_count() or 1
+    rate = oracle_rate(o, cores)
+    nbytes = int(min(64 * MIB, max(MIB, rate * seconds / 2))) // 16 * 16
+    data = wl.random_bytes(nbytes, 91)
+    key = wl.random_key(keybits, 91).tobytes()
+    t0 = time.perf_counter()
+    ct = o.ecb(0, key, data, nthreads=cores)
+    t1 = time.perf_counter()
+    o.ecb(1, key, ct, nthreads=cores)
+    t2 = time.perf_counter()
+    gbps = 2 * nbytes * 8 / (t2 - t0) / 1e9
+    return {"value": gbps, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"AES-{keybits} ECB encrypt+decrypt of {nbytes:,} bytes (seeded uniform random), "
+                      f"{cores} threads, contiguous split",
+            "seconds": round(t2 - t0, 3), "enc_s": round(t1 - t0, 3), "dec_s": round(t2 - t1, 3)}
+
+
+def run_reference(args, dist: Dist):
+    if dist.rank != 0:
+        return
+    import oracle
+    from paper_1902_05234_gb300 import workloads as wl
+    o = oracle.Oracle()
+    cores = os.cpu_count() or 1
+    rate = oracle_rate(o, cores)
+    budget_s = min(2.0, 150.0 / max(1, args.steps + args.warmup))
+    nbytes = max(16 * 1024, int(rate * budget_s / 2) // 16 * 16)
+    data = wl.random_bytes(nbytes, 92)
+    key = wl.random_key(args.keybits, 92).tobytes()
+    for _ in range(args.warmup):
+        o.ecb(1, key, o.ecb(0, key, data, nthreads=cores), nthreads=cores)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        o.ecb(1, key, o.ecb(0, key, data, nthreads=cores), nthreads=cores)
+    dt = time.perf_counter() - t
+    ms = dt / args.steps * 1e3
+    gbps = 2 * nbytes * 8 * args.steps / dt / 1e9
+    sample = (f"each step: AES-{args.keybits} ECB encrypt+decrypt of {nbytes:,} bytes of the workload's "
+              f"distribution on {cores} host threads")
+    line = {"metric": METRIC, "value": gbps, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": workload_config(args, args.gpus),
+            "cpu_baseline": {"value": gbps, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": gbps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GB300 arm
+# ---------------------------------------------------------------------------
+
+def timed_ecb(torch, aesgb, rk, nr, direction, src, dst, nblocks, iters=5, warm=2):
+    for _ in range(warm):
+        (aesgb.aes_ecb_encrypt if direction == 0 else aesgb.aes_ecb_decrypt)(rk, nr, src, dst, nblocks)
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(iters):
+        (aesgb.aes_ecb_encrypt if direction == 0 else aesgb.aes_ecb_decrypt)(rk, nr, src, dst, nblocks)
+    e.record()
+    e.synchronize()
+    return s.elapsed_time(e) / iters
+
+
+def run_sweep(torch, aesgb, dev):
+    """Single-buffer sweep: 1 MiB .. 4 GiB (powers of 4) x key sizes x directions."""
+    from paper_1902_05234_gb300 import workloads as wl
+    sizes = [MIB * 4 ** i for i in range(7)]
+    big = sizes[-1]
+    src = torch.empty(big, dtype=torch.uint8, device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(wl.BASE_SEED + 20)
+    src.random_(0, 256, generator=g)
+    dst = torch.empty_like(src)
+    rows = []
+    for kb in (128, 192, 256):
+        enc, dec, nr = aesgb.aes_expand_key(kb, wl.random_key(kb, 20).tobytes())
+        for d in (0, 1):
+            for sz in sizes:
+                n = sz // 16
+                iters = 5 if sz >= 256 * MIB else 20
+                ms = timed_ecb(torch, aesgb, enc if d == 0 else dec, nr, d, src, dst, n, iters=iters)
+                rows.append({"keybits": kb, "dir": "enc" if d == 0 else "dec", "bytes": sz,
+                             "ms": round(ms, 4), "gbps": round(sz * 8 / ms / 1e6, 1)})
+    del src, dst
+    torch.cuda.empty_cache()
+    return rows
+
+
+def run_gb300(args, dist: Dist):
+    import torch
+    from paper_1902_05234_gb300 import aesgb
+    from paper_1902_05234_gb300 import workloads as wl
+
+    dev = torch.device("cuda", dist.local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    nbytes = args.bytes // 16 * 16
+    nblocks = nbytes // 16
+    key = wl.random_key(args.keybits, 30 + dist.rank).tobytes()
+
+    pt = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(wl.BASE_SEED + 30 + dist.rank)
+    pt.random_(0, 256, generator=g)
+    ct = torch.empty_like(pt)
+    back = torch.empty_like(pt)
+
+    def step(ev=None, k=0):
+        enc, dec, nr = aesgb.aes_expand_key(args.keybits, key)
+        if ev is not None:
+            ev[0][k].record(stream)
+        aesgb.aes_ecb_encrypt(enc, nr, pt, ct, nblocks, stream)
+        if ev is not None:
+            ev[1][k].record(stream)
+        aesgb.aes_ecb_decrypt(dec, nr, ct, back, nblocks, stream)
+        if ev is not None:
+            ev[2][k].record(stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if not torch.equal(back, pt):
+        raise SystemExit("bench: decrypt(encrypt(x)) != x")
+
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(K)] for _ in range(3)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dist.local)
+    clocks.start()
+    dist.barrier()
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for k in range(K):
+        step(evs, k)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    enc_ms = statistics.mean(evs[0][k].elapsed_time(evs[1][k]) for k in range(K))
+    dec_ms = statistics.mean(evs[1][k].elapsed_time(evs[2][k]) for k in range(K))
+    if not torch.equal(back, pt):
+        raise SystemExit("bench: decrypt(encrypt(x)) != x after the timed steps")
+
+    max_ms = dist.max(total_ms)
+    ms_per_step = max_ms / K
+    world = dist.world
+    bits_per_step = 2 * nbytes * 8 * world
+    value = bits_per_step / (ms_per_step / 1e3) / 1e9
+    clk = clocks.summary()
+
+    # --- roofline of the encryption kernel --------------------------------
+    nr = nrounds_of(args.keybits)
+    sms = aesgb.aes_device_sm_count(dist.local)
+    f_mhz = clk["sm_mhz"] or 2070.0
+    lookup_bytes = nblocks * 16 * nr * 4                 # algorithmic smem lookup bytes per launch
+    achieved_gbs = lookup_bytes / (enc_ms / 1e3) / 1e9
+    peak_gbs = sms * f_mhz * 1e6 * 128 / 1e9             # 32 banks x 4 B per clock per SM
+    peak_gbps_metric = sms * f_mhz * 1e6 * 256 / nr / 1e9
+    enc_gbps = nbytes * 8 / enc_ms / 1e6
+    dec_gbps = nbytes * 8 / dec_ms / 1e6
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    roofline = {
+        "bound": "smem", "kernel": f"ecb_kernel<encrypt,Nr={nr}>",
+        "achieved": round(achieved_gbs, 1), "peak": round(peak_gbs, 1), "unit": "GB/s",
+        "frac": round(achieved_gbs / peak_gbs, 4),
+        "traffic": recorded_traffic("ecb_encrypt", args.keybits, nbytes),
+        "algorithmic_bytes_per_launch": lookup_bytes,
+        "peak_basis": f"{sms} SMs x {f_mhz:.0f} MHz (median sampled under load) x 128 B/clk shared-memory "
+                      f"lookups (derived from unit counts and the measured clock)",
+        "achieved_gbps": round(enc_gbps, 1), "peak_gbps": round(peak_gbps_metric, 1),
+        "avg_launch_ms": round(enc_ms, 4),
+        "hbm": {"achieved_gbs": round(2 * nbytes / (enc_ms / 1e3) / 1e9, 1), "peak_gbs": hbm_peak,
+                "frac": round(2 * nbytes / (enc_ms / 1e3) / 1e9 / hbm_peak, 4), "peak_source": "measured"},
+        "decrypt": {"avg_launch_ms": round(dec_ms, 4), "gbps": round(dec_gbps, 1),
+                    "frac": round(lookup_bytes / (dec_ms / 1e3) / 1e9 / peak_gbs, 4)},
+    }
+
+    # --- end to end through the host-buffer entry point --------------------
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(torch, aesgb, key, args.keybits, pt, nbytes, stream, dist, K)
+
+    line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": workload_config(args, world),
+            "enc_gbps": round(enc_gbps, 1), "dec_gbps": round(dec_gbps, 1),
+            "roofline": roofline, "e2e": e2e, "gpu_launches": 2 * K * world,
+            "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")} | {"samples": clk["samples"]},
+            "launch_cfg": repr(aesgb.aes_ecb_get_cfg(0, nr, nblocks))}
+    del ct, back
+    torch.cuda.empty_cache()
+    if dist.rank == 0 and world == 1 and not args.no_sweep:
+        line["sweep"] = run_sweep(torch, aesgb, dev)
+    if dist.rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(args.keybits)
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_e2e(torch, aesgb, key, keybits, pt_dev, nbytes, stream, dist, K):
+    """Host plaintext -> encrypt -> host ciphertext -> decrypt -> host plaintext,
+    all through aes_ecb_host with page-locked host buffers."""
+    nblocks = nbytes // 16
+    h_pt = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    h_ct = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    h_back = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    h_pt.copy_(pt_dev)
+    stage_bytes = 3 * 64 * MIB
+    stage = torch.empty(stage_bytes, dtype=torch.uint8, device=pt_dev.device)
+
+    def e2e_step():
+        enc, dec, nr = aesgb.aes_expand_key(keybits, key)
+        aesgb.aes_ecb_host(0, enc, nr, h_pt, h_ct, nblocks, stage, stage_bytes, stream)
+        aesgb.aes_ecb_host(1, dec, nr, h_ct, h_back, nblocks, stage, stage_bytes, stream)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    iters = max(3, min(K, 10))
+    dist.barrier()
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    s.record(stream)
+    for _ in range(iters):
+        e2e_step()
+    e.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    ms = dist.max(s.elapsed_time(e)) / iters
+    if not torch.equal(h_back, h_pt):
+        raise SystemExit("bench e2e: decrypt(encrypt(x)) != x")
+    return {"value": round(2 * nbytes * 8 * dist.world / ms / 1e6, 2), "unit": UNIT,
+            "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": 2 * nbytes,
+            "ms_per_step": round(ms, 4), "api": "aes_ecb_host (3 x 64 MiB staging slots)",
+            "steps": iters}
+
+
+def main():
+    args = parse_args()
+    dist = Dist()
+    try:
+        if args.impl == "reference":
+            run_reference(args, dist)
+        else:
+            run_gb300(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -134,6 +134,32 @@ int aes_ecb_crypt_cfg(int dir, const uint32_t *rk, int nrounds, const uint8_t *i
 /* The configuration aes_ecb_encrypt/decrypt would use for this call. */
 int aes_ecb_get_cfg(int dir, int nrounds, size_t nblocks, aes_launch_cfg *cfg);
 
+/* ECB over HOST buffers: the path a caller takes whose data is in host
+ * memory.  Same cipher as aes_ecb_encrypt/decrypt (dir 0 = encrypt with
+ * rk_enc, 1 = decrypt with rk_dec; rk HOST, copied during the call).
+ *   host_in, host_out  HOST, nblocks*16 bytes; equal (in place) or disjoint.
+ *                      Page-locked memory (cudaHostAlloc / cudaHostRegister)
+ *                      lets the copies overlap the kernels; pageable memory
+ *                      works but the copies then serialise.
+ *   dev_buf            DEVICE staging buffer, caller-owned, 16-byte aligned,
+ *                      dev_buf_bytes >= 48; it is split into 3 slots and the
+ *                      data moves through it in chunks of dev_buf_bytes/3.
+ * The chunks are copied in, ciphered in place and copied out on three
+ * streams the library creates on the first call per device (released by
+ * aes_shutdown), so copies and kernels of successive chunks overlap.  The
+ * call is asynchronous: `stream` first waits for its earlier work, then is
+ * made to wait for the last copy-out, so synchronising `stream` means the
+ * result is in host_out.  Host buffers and dev_buf must stay valid until
+ * then.  Calls on one device are serialised on the internal streams. */
+int aes_ecb_host(int dir, const uint32_t *rk, int nrounds, const uint8_t *host_in,
+                 uint8_t *host_out, size_t nblocks, uint8_t *dev_buf, size_t dev_buf_bytes,
+                 void *stream);
+
+/* Release every resource the library created lazily (internal streams and
+ * events, batch workspaces, tuner state) on all devices.  Call with no work
+ * of the library in flight. */
+int aes_shutdown(void);
+
 /* ------------------------------------------------------------------------ */
 /* Introspection                                                             */
 /* ------------------------------------------------------------------------ */

@@ -69,6 +69,8 @@ _SIGNATURES = {
     "aes_ecb_get_cfg": (_i, [_i, _i, _sz, ctypes.POINTER(aes_launch_cfg)]),
     "aes_device_sm_count": (_i, [_i]),
     "aes_host_table": (_i, [_i, _u32p]),
+    "aes_ecb_host": (_i, [_i, _u32p, _i, _vp, _vp, _sz, _vp, _sz, _vp]),
+    "aes_shutdown": (_i, []),
     "aes_device_table": (_i, [_i, _u32p]),
 }
 
@@ -214,6 +216,17 @@ def aes_device_table(which: int) -> np.ndarray:
     out = np.zeros(256, np.uint32)
     _check(lib().aes_device_table(int(which), out.ctypes.data_as(_u32p)), "aes_device_table")
     return out
+
+
+def aes_ecb_host(direction: int, rk, nrounds: int, host_in, host_out, nblocks: int, dev_buf,
+                 dev_buf_bytes: int, stream=None) -> None:
+    p, _keep = _rk_arg(rk)
+    _check(lib().aes_ecb_host(int(direction), p, int(nrounds), _ptr(host_in), _ptr(host_out), int(nblocks),
+                              _ptr(dev_buf), int(dev_buf_bytes), _stream(stream)), "aes_ecb_host")
+
+
+def aes_shutdown() -> None:
+    _check(lib().aes_shutdown(), "aes_shutdown")
 
 
 # ---------------------------------------------------------------------------

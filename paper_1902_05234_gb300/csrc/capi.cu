@@ -226,6 +226,11 @@ int aes_host_table(int which, uint32_t *out) {
     return AES_OK;
 }
 
+int aes_shutdown(void) {
+    host_io_shutdown();
+    return AES_OK;
+}
+
 int aes_device_table(int which, uint32_t *out) {
     if (!out || which < 0 || which > 3) return AES_E_ARG;
     return ecb_module_const_table(which, out) == 0 ? AES_OK : AES_E_CUDA;

@@ -24,6 +24,11 @@ int launch_ecb(int dir, const uint32_t *rk, int nr, const uint8_t *in, uint8_t *
 // keysched.cpp
 int expand_key_host(int keybits, const uint8_t *key, uint32_t *rk_enc, uint32_t *rk_dec);
 
+// host_io.cpp
+int host_pipeline(int dir, const uint32_t *rk, int nr, const uint8_t *hin, uint8_t *hout, size_t nblocks,
+                  uint8_t *dbuf, size_t dbuf_bytes, void *stream);
+void host_io_shutdown();
+
 // tune.cpp
 aes_launch_cfg default_cfg(int dir, int nrounds, size_t nblocks);
 aes_launch_cfg tuned_or_default_cfg(int dir, int nrounds, size_t nblocks);

@@ -136,3 +136,30 @@ def test_tensor_convenience_roundtrip(orc):
     torch.cuda.synchronize()
     assert np.array_equal(c.cpu().numpy(), oracle_ecb(orc, 0, key, data))
     assert torch.equal(p, x)
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffer_pipeline(orc, pinned):
+    """aes_ecb_host: host in -> staging chunks -> host out, several chunks and
+    a ragged last chunk; both directions; in place on the host buffer."""
+    torch = torch_cuda()
+    key = wl.random_key(256, 8).tobytes()
+    enc, dec, nr = aesgb.aes_expand_key(256, key)
+    n = 100_003
+    data = wl.random_bytes(16 * n, 13)
+    h_in = torch.from_numpy(data.copy())
+    h_out = torch.zeros_like(h_in)
+    if pinned:
+        h_in, h_out = h_in.pin_memory(), h_out.pin_memory()
+    stage_bytes = 3 * 16 * 4099            # 4,099-block slots: 25 chunks, the last one partial
+    stage = torch.empty(stage_bytes, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream()
+    aesgb.aes_ecb_host(0, enc, nr, h_in, h_out, n, stage, stage_bytes, s)
+    s.synchronize()
+    exp = oracle_ecb(orc, 0, key, data)
+    assert np.array_equal(h_out.numpy(), exp)
+    aesgb.aes_ecb_host(1, dec, nr, h_out, h_out, n, stage, stage_bytes, s)   # in place
+    s.synchronize()
+    assert np.array_equal(h_out.numpy(), data)
+    with pytest.raises(aesgb.AesError):
+        aesgb.aes_ecb_host(0, enc, nr, h_in, h_out, n, stage, 32, s)          # staging too small
