@@ -57,6 +57,7 @@ def parse_args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-sweep", action="store_true")
+    p.add_argument("--no-batched", action="store_true")
     return p.parse_args()
 
 
@@ -319,6 +320,111 @@ def run_sweep(torch, aesgb, dev):
     return rows
 
 
+def run_batched(torch, aesgb, dev, n=4096):
+    """Batched workload: 4,096 messages, log-uniform 16 B .. 16 MiB, key size
+    uniform over {128,192,256}, direction 50/50 -- one persistent launch from a
+    device descriptor table replayed as a CUDA graph, against the same messages
+    as one aes_ecb_encrypt/decrypt launch each (the loop a user of the plain
+    API writes), both as a CUDA-graph replay of the launches and as a Python
+    loop with the key schedule per message."""
+    import numpy as np
+    from paper_1902_05234_gb300 import workloads as wl
+    lengths, keybits, dirs = wl.batch_workload(n)
+    offs = np.zeros(n + 1, np.int64)
+    np.cumsum(lengths, out=offs[1:])
+    total = int(offs[-1])
+    src = torch.empty(total, dtype=torch.uint8, device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(wl.BASE_SEED + 40)
+    src.random_(0, 256, generator=g)
+    dst = torch.empty_like(src)
+    ref = torch.empty_like(src)
+    kg = wl.rng(40)
+    keys = [kg.integers(0, 256, int(kb) // 8, dtype=np.uint8).tobytes() for kb in keybits]
+    rks = np.zeros((n, 64), np.uint32)
+    host_rk, nrs = [], np.zeros(n, np.int64)
+    for i in range(n):
+        enc, dec, nr = aesgb.aes_expand_key(int(keybits[i]), keys[i])
+        rk = enc if dirs[i] == 0 else dec
+        rks[i, :60] = rk
+        host_rk.append(rk)
+        nrs[i] = nr
+    rk_dev = torch.from_numpy(rks.view(np.uint8).reshape(-1)).to(dev)
+    table = aesgb.pack_descs(rk_dev.data_ptr() + 256 * np.arange(n, dtype=np.uint64),
+                             src.data_ptr() + offs[:-1].astype(np.uint64),
+                             dst.data_ptr() + offs[:-1].astype(np.uint64), lengths // 16, nrs, dirs)
+    desc = torch.from_numpy(table.view(np.uint8).copy()).to(dev)
+    ws_bytes = aesgb.aes_batch_workspace_bytes(n)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def ev_time(fn, iters):
+        s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s_.record(stream)
+        for _ in range(iters):
+            fn()
+        e_.record(stream)
+        e_.synchronize()
+        return s_.elapsed_time(e_) / iters
+
+    graph = aesgb.aes_batch_graph_create(desc, n, ws, ws_bytes)
+    try:
+        for _ in range(2):
+            aesgb.aes_batch_graph_launch(graph, stream)
+        ms_batch = ev_time(lambda: aesgb.aes_batch_graph_launch(graph, stream), 5)
+    finally:
+        aesgb.aes_batch_graph_destroy(graph)
+
+    def loop_launches(strm):
+        for i in range(n):
+            nb = int(lengths[i]) // 16
+            a, b = src.data_ptr() + int(offs[i]), ref.data_ptr() + int(offs[i])
+            if dirs[i] == 0:
+                aesgb.aes_ecb_encrypt(host_rk[i], int(nrs[i]), a, b, nb, strm)
+            else:
+                aesgb.aes_ecb_decrypt(host_rk[i], int(nrs[i]), a, b, nb, strm)
+
+    loop_launches(stream)
+    torch.cuda.synchronize()
+    same = bool(torch.equal(dst, ref))
+    cap = torch.cuda.Stream()
+    lg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(lg, stream=cap, capture_error_mode="relaxed"):
+        loop_launches(cap)
+    lg.replay()
+    torch.cuda.synchronize()
+    ms_loop_graph = ev_time(lg.replay, 3)
+    del lg
+
+    def py_loop():
+        for i in range(n):
+            enc, dec, nr = aesgb.aes_expand_key(int(keybits[i]), keys[i])
+            nb = int(lengths[i]) // 16
+            a, b = src.data_ptr() + int(offs[i]), ref.data_ptr() + int(offs[i])
+            if dirs[i] == 0:
+                aesgb.aes_ecb_encrypt(enc, nr, a, b, nb, stream)
+            else:
+                aesgb.aes_ecb_decrypt(dec, nr, a, b, nb, stream)
+    py_loop()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    py_loop()
+    torch.cuda.synchronize()
+    ms_loop_py = (time.perf_counter() - t) * 1e3
+    gb = total * 8 / 1e9
+    out = {"workload": f"{n} messages, log-uniform 16 B..16 MiB (total {total:,} B), keys uniform over "
+                       f"128/192/256, direction 50/50",
+           "total_bytes": total, "ms": round(ms_batch, 4), "gbps": round(gb / (ms_batch / 1e3), 1),
+           "loop_graph_ms": round(ms_loop_graph, 4), "loop_graph_gbps": round(gb / (ms_loop_graph / 1e3), 1),
+           "loop_python_ms": round(ms_loop_py, 3), "loop_python_gbps": round(gb / (ms_loop_py / 1e3), 1),
+           "speedup_vs_loop_graph": round(ms_loop_graph / ms_batch, 3),
+           "speedup_vs_loop_python": round(ms_loop_py / ms_batch, 3),
+           "identical_to_loop": same, "cfg": repr(aesgb.make_batch_cfg())}
+    del src, dst, ref, rk_dev, desc, ws
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_gb300(args, dist: Dist):
     import torch
     from paper_1902_05234_gb300 import aesgb
@@ -429,6 +535,8 @@ def run_gb300(args, dist: Dist):
     torch.cuda.empty_cache()
     if dist.rank == 0 and world == 1 and not args.no_sweep:
         line["sweep"] = run_sweep(torch, aesgb, dev)
+    if dist.rank == 0 and world == 1 and not args.no_batched:
+        line["batched"] = run_batched(torch, aesgb, dev)
     if dist.rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.keybits)
     if dist.rank == 0:

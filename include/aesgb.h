@@ -134,6 +134,74 @@ int aes_ecb_crypt_cfg(int dir, const uint32_t *rk, int nrounds, const uint8_t *i
 /* The configuration aes_ecb_encrypt/decrypt would use for this call. */
 int aes_ecb_get_cfg(int dir, int nrounds, size_t nblocks, aes_launch_cfg *cfg);
 
+/* ------------------------------------------------------------------------ */
+/* Batched ECB: many messages, one persistent launch                         */
+/* ------------------------------------------------------------------------ */
+
+/* One message of a batch: ECB (eq (1)) over nblocks blocks with its own key,
+ * key size and direction.  The descriptor table lives in DEVICE memory.
+ *   rk       DEVICE, 4*(nrounds+1) words: rk_enc for dir 0, rk_dec (FIPS dw
+ *            order, exactly as aes_expand_key writes it) for dir 1.
+ *   in, out  DEVICE, 16-byte aligned; equal or disjoint.  Outputs of different
+ *            messages must not overlap each other or any input.
+ *   nblocks  may be 0 (nothing to do).
+ *   nrounds  10, 12 or 14.   dir  0 encrypt, 1 decrypt.
+ * A descriptor that breaks these rules is skipped (its output untouched) and
+ * its status (AES_E_NROUNDS, AES_E_ARG, AES_E_ALIGN, AES_E_OVERLAP) is written
+ * to the optional status array; the other messages are processed. */
+typedef struct aes_desc {
+    const uint32_t *rk;
+    const uint8_t *in;
+    uint8_t *out;
+    uint64_t nblocks;
+    int32_t nrounds;
+    int32_t dir;
+} aes_desc;
+
+/* Launch configuration of the batch kernel (tables always bank-replicated). */
+typedef struct aes_batch_cfg {
+    int32_t threads;           /* threads per CTA (multiple of 32, <= 512: keys sit in registers)    */
+    int32_t blocks_per_thread; /* 1, 2 or 4                                                           */
+    int32_t chunk_passes;      /* a warp's unit of work = 32 * blocks_per_thread * chunk_passes blocks */
+    int32_t ctas_per_sm;       /* 0 or 1 (the tables take most of the shared memory)                */
+} aes_batch_cfg;
+
+/* Bytes of DEVICE workspace a batch of n descriptors needs (plan header, the
+ * message order and the chunk prefix: about 20 bytes per descriptor). */
+size_t aes_batch_workspace_bytes(int n);
+
+/* Batched ECB with a caller-owned workspace.  Enqueues two kernels on
+ * `stream`: a one-CTA plan kernel (validation, encryptions-first order, chunk
+ * prefix) and the persistent batch kernel (one CTA per SM; warp g takes chunks
+ * g, g+W, ...; a chunk's message is found by binary search; each warp stages
+ * its message's round keys in shared memory).  Allocates nothing and never
+ * synchronises, so it can be captured in a CUDA graph.
+ *   desc_dev    DEVICE array of n descriptors, unchanged until completion.
+ *   ws          DEVICE, 256-byte aligned, ws_bytes >= aes_batch_workspace_bytes(n);
+ *               owned by the caller and busy until completion.
+ *   status_dev  DEVICE int32[n] or NULL: per-message aes_status.
+ *   cfg         NULL for the tuned/default configuration.
+ * Returns AES_E_RANGE if ws is too small, AES_E_CONFIG for a bad cfg. */
+int aes_ecb_batch_ws(const aes_desc *desc_dev, int n, void *ws, size_t ws_bytes, int32_t *status_dev,
+                     const aes_batch_cfg *cfg, void *stream);
+
+/* Batched ECB with a library-owned workspace: the same as aes_ecb_batch_ws
+ * with a per-device workspace the library allocates on first use and grows
+ * (cudaMalloc; the growth synchronises the device) when n exceeds it; freed by
+ * aes_shutdown.  Concurrent batches on different streams of one device must
+ * use aes_ecb_batch_ws with distinct workspaces. */
+int aes_ecb_batch(const aes_desc *desc_dev, int n, void *stream);
+
+/* A batch captured once as a CUDA graph (plan + batch kernel) and replayed.
+ * desc_dev, ws and status_dev are baked in; the CONTENTS of the descriptor
+ * table may change between launches (the plan kernel reads it at run time),
+ * n may not.  aes_batch_graph_launch enqueues one replay on `stream`. */
+typedef struct aes_batch_graph aes_batch_graph;
+int aes_batch_graph_create(const aes_desc *desc_dev, int n, void *ws, size_t ws_bytes, int32_t *status_dev,
+                           const aes_batch_cfg *cfg, aes_batch_graph **graph);
+int aes_batch_graph_launch(aes_batch_graph *graph, void *stream);
+int aes_batch_graph_destroy(aes_batch_graph *graph);
+
 /* ECB over HOST buffers: the path a caller takes whose data is in host
  * memory.  Same cipher as aes_ecb_encrypt/decrypt (dir 0 = encrypt with
  * rk_enc, 1 = decrypt with rk_dec; rk HOST, copied during the call).

@@ -53,6 +53,21 @@ class aes_desc(ctypes.Structure):
                 ("nblocks", ctypes.c_uint64), ("nrounds", ctypes.c_int32), ("dir", ctypes.c_int32)]
 
 
+class aes_batch_cfg(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("blocks_per_thread", ctypes.c_int32),
+                ("chunk_passes", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+
+    def __repr__(self):
+        return (f"aes_batch_cfg(threads={self.threads}, bpt={16 * self.blocks_per_thread}B, "
+                f"chunk_passes={self.chunk_passes}, ctas_per_sm={self.ctas_per_sm})")
+
+
+# numpy view of aes_desc (40 bytes) for building descriptor tables in bulk
+DESC_DTYPE = np.dtype([("rk", "<u8"), ("in", "<u8"), ("out", "<u8"), ("nblocks", "<u8"),
+                       ("nrounds", "<i4"), ("dir", "<i4")])
+assert DESC_DTYPE.itemsize == ctypes.sizeof(aes_desc) == 40
+
+
 _vp = ctypes.c_void_p
 _sz = ctypes.c_size_t
 _u32p = ctypes.POINTER(ctypes.c_uint32)
@@ -70,6 +85,12 @@ _SIGNATURES = {
     "aes_device_sm_count": (_i, [_i]),
     "aes_host_table": (_i, [_i, _u32p]),
     "aes_ecb_host": (_i, [_i, _u32p, _i, _vp, _vp, _sz, _vp, _sz, _vp]),
+    "aes_batch_workspace_bytes": (_sz, [_i]),
+    "aes_ecb_batch_ws": (_i, [_vp, _i, _vp, _sz, _vp, _vp, _vp]),
+    "aes_ecb_batch": (_i, [_vp, _i, _vp]),
+    "aes_batch_graph_create": (_i, [_vp, _i, _vp, _sz, _vp, _vp, ctypes.POINTER(_vp)]),
+    "aes_batch_graph_launch": (_i, [_vp, _vp]),
+    "aes_batch_graph_destroy": (_i, [_vp]),
     "aes_shutdown": (_i, []),
     "aes_device_table": (_i, [_i, _u32p]),
 }
@@ -227,6 +248,50 @@ def aes_ecb_host(direction: int, rk, nrounds: int, host_in, host_out, nblocks: i
 
 def aes_shutdown() -> None:
     _check(lib().aes_shutdown(), "aes_shutdown")
+
+
+def aes_batch_workspace_bytes(n: int) -> int:
+    return int(lib().aes_batch_workspace_bytes(int(n)))
+
+
+def aes_ecb_batch_ws(desc_dev, n: int, ws, ws_bytes: int, status_dev=None, cfg: aes_batch_cfg | None = None,
+                     stream=None) -> None:
+    _check(lib().aes_ecb_batch_ws(_ptr(desc_dev), int(n), _ptr(ws), int(ws_bytes), _ptr(status_dev),
+                                  ctypes.addressof(cfg) if cfg is not None else None, _stream(stream)),
+           "aes_ecb_batch_ws")
+
+
+def aes_ecb_batch(desc_dev, n: int, stream=None) -> None:
+    _check(lib().aes_ecb_batch(_ptr(desc_dev), int(n), _stream(stream)), "aes_ecb_batch")
+
+
+def aes_batch_graph_create(desc_dev, n: int, ws, ws_bytes: int, status_dev=None,
+                           cfg: aes_batch_cfg | None = None) -> int:
+    h = _vp()
+    _check(lib().aes_batch_graph_create(_ptr(desc_dev), int(n), _ptr(ws), int(ws_bytes), _ptr(status_dev),
+                                        ctypes.addressof(cfg) if cfg is not None else None, ctypes.byref(h)),
+           "aes_batch_graph_create")
+    return int(h.value)
+
+
+def aes_batch_graph_launch(graph: int, stream=None) -> None:
+    _check(lib().aes_batch_graph_launch(_vp(graph), _stream(stream)), "aes_batch_graph_launch")
+
+
+def aes_batch_graph_destroy(graph: int) -> None:
+    _check(lib().aes_batch_graph_destroy(_vp(graph)), "aes_batch_graph_destroy")
+
+
+def make_batch_cfg(threads=512, blocks_per_thread=1, chunk_passes=32, ctas_per_sm=1) -> aes_batch_cfg:
+    return aes_batch_cfg(int(threads), int(blocks_per_thread), int(chunk_passes), int(ctas_per_sm))
+
+
+def pack_descs(rk, in_, out, nblocks, nrounds, direction) -> np.ndarray:
+    """Pack parallel sequences (device addresses as ints) into an aes_desc table."""
+    t = np.zeros(len(nblocks), DESC_DTYPE)
+    t["rk"], t["in"], t["out"] = rk, in_, out
+    t["nblocks"], t["nrounds"], t["dir"] = nblocks, nrounds, direction
+    return t
 
 
 # ---------------------------------------------------------------------------

@@ -52,7 +52,10 @@ def _compile(src: str, nvcc: str) -> str:
     cmd = [nvcc, "-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC,-O2",
            "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]
     if src.endswith(".cu"):
-        cmd[1:1] = ["-Xptxas", "-warn-spills"]
+        # every nvcc/cudafe/ptxas warning is an error: a host-only helper called
+        # from device code is only a warning otherwise, and the kernel then
+        # silently compiles to nothing
+        cmd[1:1] = ["-Xptxas", "-warn-spills", "--Werror", "all-warnings"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"compile failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

@@ -1,0 +1,544 @@
+// batch.cu -- many independent ECB messages, each with its own key, key size
+// and direction, in ONE persistent launch driven by a device descriptor table.
+//
+// The paper's unit of parallelism is one AES state (section 4.1, eq (1)); a
+// batch only changes which key and which buffer a state belongs to, never the
+// arithmetic.  Two kernels run back to back on the caller's stream:
+//
+//  plan   (one CTA)  validates every descriptor (bad ones get a status and no
+//                    work), orders the messages encryptions first, and writes
+//                    the exclusive prefix `start[]` of their chunk counts,
+//                    where a chunk is `chunk_blocks` consecutive blocks of one
+//                    message -- the work of one warp.
+//  batch  (persistent, one CTA per SM)  warps take chunks of the encryption
+//                    range, then of the decryption range, from two atomic
+//                    counters (dynamic: whichever warp is free takes the next
+//                    chunk).  A chunk's message is found by a warp-wide 32-ary
+//                    search in start[]; its round keys are staged through the
+//                    warp's own shared-memory slot into registers.  The CTA's T tables are filled for
+//                    encryption first and refilled once for decryption, between
+//                    two CTA barriers that every warp reaches.
+//
+// Workspace layout (caller- or library-owned device memory, see
+// aes_batch_workspace_bytes):
+//   BatchHeader | uint32 order[n] | uint64 start[n+1] | uint64 count[n]
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <mutex>
+
+#include "aesgb.h"
+#include "aes_kernels.cuh"
+#include "batch_internal.h"
+#include "capi_internal.h"
+
+namespace aesgb {
+
+static_assert(sizeof(aes_desc) == 40, "aes_desc is 40 bytes");
+static_assert(offsetof(aes_desc, nblocks) == 24 && offsetof(aes_desc, nrounds) == 32 &&
+                  offsetof(aes_desc, dir) == 36,
+              "aes_desc field offsets");
+
+struct BatchHeader {
+    unsigned long long total_chunks;  // T
+    unsigned long long enc_chunks;    // E: chunks [0, E) encrypt, [E, T) decrypt
+    unsigned long long next[2];       // work counters of the two phases (zeroed by the plan)
+    unsigned int n;
+    unsigned int chunk_blocks;
+    unsigned int n_invalid;
+    unsigned int pad;
+};
+
+__host__ __device__ constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+size_t batch_ws_bytes(int n) {
+    const size_t nn = n > 0 ? static_cast<size_t>(n) : 0;
+    return align_up(sizeof(BatchHeader), 256) + align_up(4 * nn, 256) + align_up(8 * (nn + 1), 256) +
+           align_up(8 * nn, 256);
+}
+
+struct WsView {
+    BatchHeader *hdr;
+    uint32_t *order;
+    unsigned long long *start;
+    unsigned long long *count;
+};
+
+__host__ __device__ inline WsView ws_view(void *ws, int n) {
+    const size_t nn = static_cast<size_t>(n);
+    uint8_t *p = static_cast<uint8_t *>(ws);
+    WsView v;
+    v.hdr = reinterpret_cast<BatchHeader *>(p);
+    p += align_up(sizeof(BatchHeader), 256);
+    v.order = reinterpret_cast<uint32_t *>(p);
+    p += align_up(4 * nn, 256);
+    v.start = reinterpret_cast<unsigned long long *>(p);
+    p += align_up(8 * (nn + 1), 256);
+    v.count = reinterpret_cast<unsigned long long *>(p);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// plan kernel
+// ---------------------------------------------------------------------------
+constexpr int kPlanThreads = 1024;
+
+// Exclusive scan of one value per thread over the CTA; returns the prefix and
+// writes the CTA total to *total.
+template <typename T>
+__device__ T cta_exclusive_scan(T v, T *warp_sums, T *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        T s = lane < nw ? warp_sums[lane] : T(0);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const T y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) warp_sums[lane] = s;  // inclusive warp prefix
+    }
+    __syncthreads();
+    const T before = warp == 0 ? T(0) : warp_sums[warp - 1];
+    *total = warp_sums[nw - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__device__ int check_desc(const aes_desc &d) {
+    if (d.nrounds != 10 && d.nrounds != 12 && d.nrounds != 14) return AES_E_NROUNDS;
+    if (d.dir != 0 && d.dir != 1) return AES_E_ARG;
+    if (d.nblocks == 0) return AES_OK;
+    if (!d.rk || !d.in || !d.out) return AES_E_ARG;
+    if (d.nblocks > (~0ull >> 5)) return AES_E_ARG;
+    const unsigned long long a = reinterpret_cast<unsigned long long>(d.in),
+                             b = reinterpret_cast<unsigned long long>(d.out);
+    if (((a | b) & 15ull) || (reinterpret_cast<unsigned long long>(d.rk) & 3ull)) return AES_E_ALIGN;
+    const unsigned long long len = d.nblocks << 4;
+    if (a != b && a < b + len && b < a + len) return AES_E_OVERLAP;
+    return AES_OK;
+}
+
+__global__ void __launch_bounds__(kPlanThreads, 1)
+    batch_plan_kernel(const aes_desc *__restrict__ desc, int n, void *ws, int32_t *status,
+                      unsigned int chunk_blocks) {
+    __shared__ unsigned long long s_u64[32];
+    __shared__ unsigned int s_u32[32];
+    __shared__ unsigned int s_base[2];
+    const WsView v = ws_view(ws, n);
+
+    // pass 1: number of encryption messages (invalid ones count as encryption
+    // with no chunks, so they sit harmlessly in the first range)
+    unsigned int n_enc = 0, n_bad = 0;
+    for (int t0 = 0; t0 < n; t0 += blockDim.x) {
+        const int i = t0 + static_cast<int>(threadIdx.x);
+        unsigned int e = 0, bad = 0;
+        if (i < n) {
+            const aes_desc d = desc[i];
+            const int st = check_desc(d);
+            bad = st != AES_OK;
+            e = bad || d.dir == 0;
+            if (status) status[i] = st;
+        }
+        unsigned int tot = 0, totb = 0;
+        (void)cta_exclusive_scan<unsigned int>(e, s_u32, &tot);
+        (void)cta_exclusive_scan<unsigned int>(bad, s_u32, &totb);
+        n_enc += tot;
+        n_bad += totb;
+    }
+    // pass 2: stable partition (encryptions first) and chunk counts by position
+    if (threadIdx.x == 0) { s_base[0] = 0; s_base[1] = n_enc; }
+    __syncthreads();
+    for (int t0 = 0; t0 < n; t0 += blockDim.x) {
+        const int i = t0 + static_cast<int>(threadIdx.x);
+        unsigned int e = 0;
+        unsigned long long cnt = 0;
+        if (i < n) {
+            const aes_desc d = desc[i];
+            const bool ok = check_desc(d) == AES_OK;
+            e = !ok || d.dir == 0;
+            cnt = ok ? (d.nblocks + chunk_blocks - 1) / chunk_blocks : 0ull;
+        }
+        unsigned int tot_e = 0, tot_d = 0;
+        const unsigned int pe = cta_exclusive_scan<unsigned int>(e, s_u32, &tot_e);
+        const unsigned int pd = cta_exclusive_scan<unsigned int>(i < n ? 1u - e : 0u, s_u32, &tot_d);
+        if (i < n) {
+            const unsigned int pos = e ? s_base[0] + pe : s_base[1] + pd;
+            v.order[pos] = static_cast<uint32_t>(i);
+            v.count[pos] = cnt;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) { s_base[0] += tot_e; s_base[1] += tot_d; }
+        __syncthreads();
+    }
+    __threadfence_block();
+    __syncthreads();
+    // pass 3: exclusive prefix of the counts in partition order
+    unsigned long long run = 0;
+    for (int t0 = 0; t0 < n; t0 += blockDim.x) {
+        const int p = t0 + static_cast<int>(threadIdx.x);
+        const unsigned long long c = p < n ? v.count[p] : 0ull;
+        unsigned long long tot = 0;
+        const unsigned long long pre = cta_exclusive_scan<unsigned long long>(c, s_u64, &tot);
+        if (p < n) v.start[p] = run + pre;
+        run += tot;
+    }
+    if (threadIdx.x == 0) {
+        v.start[n] = run;
+        v.hdr->total_chunks = run;
+        v.hdr->next[0] = 0;
+        v.hdr->next[1] = 0;
+        v.hdr->n = static_cast<unsigned int>(n);
+        v.hdr->chunk_blocks = chunk_blocks;
+        v.hdr->n_invalid = n_bad;
+    }
+    // enc_chunks: start[n_enc] (or the total when every message encrypts)
+    __syncthreads();
+    if (threadIdx.x == 0) v.hdr->enc_chunks = n_enc >= static_cast<unsigned int>(n) ? run : v.start[n_enc];
+}
+
+// ---------------------------------------------------------------------------
+// batch kernel
+// ---------------------------------------------------------------------------
+struct BatchArgs {
+    const aes_desc *desc;
+    void *ws;
+    int n;
+};
+
+constexpr uint32_t kKeySlotBytes = 256;  // 60 words rounded up
+
+// Round keys of the current message held in registers for a whole chunk
+// (4*(NR+1) words; every index is a compile-time constant once the rounds
+// are unrolled, so the array stays in registers).
+template <int NR> struct RegKey {
+    uint32_t w[4 * (NR + 1)];
+    __device__ __forceinline__ uint32_t operator()(int i) const { return w[i]; }
+};
+
+// Blocks [first, first + count) of one message, as passes of 32*NB blocks per
+// warp with the next pass prefetched.  The round keys are read once per chunk
+// from the warp's shared-memory slot (16-byte broadcasts) into registers.
+template <int DIR, int NR, int NB>
+__device__ __forceinline__ void batch_chunk(const Tab<kLayoutR4, DIR> &tab, const uint32_t *kslot,
+                                            const uint4 *in, uint4 *out, unsigned long long first,
+                                            unsigned long long count, uint32_t lane) {
+    RegKey<NR> key;
+#pragma unroll
+    for (int q = 0; q < NR + 1; ++q) {
+        const uint4 v = reinterpret_cast<const uint4 *>(kslot)[q];
+        key.w[4 * q] = v.x; key.w[4 * q + 1] = v.y; key.w[4 * q + 2] = v.z; key.w[4 * q + 3] = v.w;
+    }
+    const unsigned long long end = first + count;
+    uint4 cur[NB];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        const unsigned long long b = first + lane + 32ull * i;
+        cur[i] = b < end ? ld_block(in + b) : make_uint4(0, 0, 0, 0);
+    }
+    for (unsigned long long base = first; base < end; base += 32ull * NB) {
+        uint4 nxt[NB];
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            const unsigned long long b = base + 32ull * NB + lane + 32ull * i;
+            nxt[i] = b < end ? ld_block(in + b) : make_uint4(0, 0, 0, 0);
+        }
+        uint32_t s[NB][4];
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            s[i][0] = cur[i].x; s[i][1] = cur[i].y; s[i][2] = cur[i].z; s[i][3] = cur[i].w;
+        }
+        cipher_states<DIR, NR, NB>(tab, key, s);
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            const unsigned long long b = base + lane + 32ull * i;
+            if (b < end) st_block(out + b, make_uint4(s[i][0], s[i][1], s[i][2], s[i][3]));
+            cur[i] = nxt[i];
+        }
+    }
+}
+
+// Partition position q of the message owning chunk c: the largest q in
+// [lo, n) with start[q] <= c (start[n] = T > c).  32-ary search by the whole
+// warp: each lane probes one of 31 evenly spaced positions per step.
+__device__ __forceinline__ int find_message(const unsigned long long *start, int lo, int n,
+                                            unsigned long long c, uint32_t lane) {
+    int hi = n;
+    while (hi - lo > 1) {
+        const int step = (hi - lo + 31) / 32;
+        const int q = lo + static_cast<int>(lane + 1) * step;
+        const bool le = q < hi && start[q] <= c;
+        const int k = __popc(__ballot_sync(0xffffffffu, le));
+        const int nlo = lo + k * step;
+        const int nhi = lo + (k + 1) * step;
+        lo = nlo;
+        hi = nhi < hi ? nhi : hi;
+    }
+    return lo;
+}
+
+// All chunks of one direction, handed out one at a time to whichever warp
+// asks next (an atomic counter in the workspace; the next chunk index is
+// requested before the current chunk is processed, so the atomic's latency is
+// hidden).  Chunk c of this phase is chunk c_begin + c of the partition.
+template <int DIR, int NB>
+__device__ void batch_phase(const BatchArgs &a, const WsView &v, uint8_t *smem, uint32_t *kslot,
+                            unsigned long long c_begin, unsigned long long c_end) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const Tab<kLayoutR4, DIR> tab(smem, lane);
+    unsigned long long *counter = &v.hdr->next[DIR];
+    const unsigned long long nchunks = c_end - c_begin;
+    const unsigned int cb = v.hdr->chunk_blocks;
+    const int n = a.n;
+    int p = 0;                                  // partition position of the current message
+    unsigned long long p_start = 0, p_end = 0;  // its chunk range [p_start, p_end)
+    const uint4 *in = nullptr;
+    uint4 *out = nullptr;
+    unsigned long long nb = 0;
+    int nr = 10;
+    bool have = false;
+    unsigned long long ticket = 0;
+    if (lane == 0) ticket = atomicAdd(counter, 1ull);
+    unsigned long long rel = __shfl_sync(0xffffffffu, ticket, 0);
+    while (rel < nchunks) {
+        if (lane == 0) ticket = atomicAdd(counter, 1ull);  // next chunk, consumed after this one
+        const unsigned long long c = c_begin + rel;
+        if (!have || c >= p_end) {
+            p = find_message(v.start, have ? p + 1 : 0, n, c, lane);
+            p_start = v.start[p];
+            p_end = v.start[p + 1];
+            const aes_desc d = a.desc[v.order[p]];
+            in = reinterpret_cast<const uint4 *>(d.in);
+            out = reinterpret_cast<uint4 *>(d.out);
+            nb = d.nblocks;
+            nr = d.nrounds;
+            __syncwarp();
+            const int nw = 4 * (nr + 1);
+            for (int i = static_cast<int>(lane); i < nw; i += 32) {
+                const int step = i >> 2;
+                const int src = DIR == kEncrypt ? step : nr - step;
+                kslot[i] = d.rk[4 * src + (i & 3)];
+            }
+            __syncwarp();
+            have = true;
+        }
+        const unsigned long long first = (c - p_start) * cb;
+        const unsigned long long cnt = nb - first < cb ? nb - first : cb;
+        switch (nr) {
+        case 10: batch_chunk<DIR, 10, NB>(tab, kslot, in, out, first, cnt, lane); break;
+        case 12: batch_chunk<DIR, 12, NB>(tab, kslot, in, out, first, cnt, lane); break;
+        default: batch_chunk<DIR, 14, NB>(tab, kslot, in, out, first, cnt, lane); break;
+        }
+        rel = __shfl_sync(0xffffffffu, ticket, 0);
+    }
+}
+
+constexpr int kBatchMaxThreads = 512;  // up to 128 registers: round keys live in registers
+
+template <int NB>
+__global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(const __grid_constant__ BatchArgs a) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    const WsView v = ws_view(a.ws, a.n);
+    const unsigned long long T = v.hdr->total_chunks, E = v.hdr->enc_chunks;
+    uint32_t *kslot = reinterpret_cast<uint32_t *>(smem + table_smem_bytes(kDecrypt, kLayoutR4) +
+                                                   (threadIdx.x >> 5) * kKeySlotBytes);
+    if (E > 0) {
+        Tab<kLayoutR4, kEncrypt>::fill(smem, threadIdx.x, blockDim.x);
+        __syncthreads();
+        batch_phase<kEncrypt, NB>(a, v, smem, kslot, 0, E);
+    }
+    if (T > E) {
+        __syncthreads();  // every warp is done with the encryption tables
+        Tab<kLayoutR4, kDecrypt>::fill(smem, threadIdx.x, blockDim.x);
+        __syncthreads();
+        batch_phase<kDecrypt, NB>(a, v, smem, kslot, E, T);
+    }
+}
+
+uint32_t batch_smem_bytes(int threads) {
+    return table_smem_bytes(kDecrypt, kLayoutR4) + static_cast<uint32_t>(threads / 32) * kKeySlotBytes;
+}
+
+const void *batch_kernel_ptr(int nb) {
+    switch (nb) {
+    case 1: return reinterpret_cast<const void *>(&batch_kernel<1>);
+    case 2: return reinterpret_cast<const void *>(&batch_kernel<2>);
+    case 4: return reinterpret_cast<const void *>(&batch_kernel<4>);
+    default: return nullptr;
+    }
+}
+
+int validate_batch_cfg(const aes_batch_cfg &c) {
+    if (c.blocks_per_thread != 1 && c.blocks_per_thread != 2 && c.blocks_per_thread != 4) return AES_E_CONFIG;
+    if (c.threads < 32 || c.threads % 32 || c.threads > kBatchMaxThreads) return AES_E_CONFIG;
+    if (c.chunk_passes < 1 || c.chunk_passes > 1024) return AES_E_CONFIG;
+    if (c.ctas_per_sm < 0 || c.ctas_per_sm > 1) return AES_E_CONFIG;
+    return AES_OK;
+}
+
+int enqueue_batch(const aes_desc *desc, int n, void *ws, size_t ws_bytes, int32_t *status,
+                  const aes_batch_cfg &c, cudaStream_t s) {
+    if (n == 0) return AES_OK;
+    if (!desc || !ws) return AES_E_ARG;
+    if (ws_bytes < batch_ws_bytes(n)) return AES_E_RANGE;
+    if (reinterpret_cast<uintptr_t>(ws) & 255u) return AES_E_ALIGN;
+    int st = validate_batch_cfg(c);
+    if (st != AES_OK) return st;
+    int dev = 0;
+    if (current_device(&dev) != AES_OK) return AES_E_CUDA;
+    const unsigned int chunk_blocks = static_cast<unsigned int>(32 * c.blocks_per_thread * c.chunk_passes);
+    batch_plan_kernel<<<1, kPlanThreads, 0, s>>>(desc, n, ws, status, chunk_blocks);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return AES_E_CUDA;
+    const void *fn = batch_kernel_ptr(c.blocks_per_thread);
+    const uint32_t smem = batch_smem_bytes(c.threads);
+    st = ensure_smem_attr(fn, dev, smem);
+    if (st != AES_OK) return st;
+    const int sms = sm_count(dev);
+    if (sms < 0) return sms;
+    BatchArgs args{desc, ws, n};
+    void *params[] = {&args};
+    e = cudaLaunchKernel(fn, dim3(sms), dim3(c.threads), params, smem, s);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return AES_E_CUDA;
+    }
+    return AES_OK;
+}
+
+// ---------------------------------------------------------------------------
+// library-owned workspace for aes_ecb_batch (grown on demand, per device)
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kMaxDev = 64;
+struct LibWs {
+    std::mutex mu;
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+LibWs g_ws[kMaxDev];
+}  // namespace
+
+int lib_workspace(int dev, size_t need, void **ptr) {
+    LibWs &w = g_ws[dev];
+    std::lock_guard<std::mutex> lk(w.mu);
+    if (w.bytes < need) {
+        if (w.ptr) {
+            if (cudaDeviceSynchronize() != cudaSuccess) return AES_E_CUDA;  // the old one may be in use
+            cudaFree(w.ptr);
+            w.ptr = nullptr;
+            w.bytes = 0;
+        }
+        size_t sz = need < (1u << 20) ? (1u << 20) : need * 2;
+        if (cudaMalloc(&w.ptr, sz) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return AES_E_NOMEM;
+        }
+        w.bytes = sz;
+    }
+    *ptr = w.ptr;
+    return AES_OK;
+}
+
+void batch_shutdown() {
+    for (int d = 0; d < kMaxDev; ++d) {
+        std::lock_guard<std::mutex> lk(g_ws[d].mu);
+        if (g_ws[d].ptr) cudaFree(g_ws[d].ptr);
+        g_ws[d].ptr = nullptr;
+        g_ws[d].bytes = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// graph: plan + batch captured once, replayed many times
+// ---------------------------------------------------------------------------
+struct BatchGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace aesgb
+
+using namespace aesgb;
+
+extern "C" {
+
+size_t aes_batch_workspace_bytes(int n) { return n < 0 ? 0 : batch_ws_bytes(n); }
+
+int aes_ecb_batch_ws(const aes_desc *desc_dev, int n, void *ws, size_t ws_bytes, int32_t *status_dev,
+                     const aes_batch_cfg *cfg, void *stream) {
+    if (n < 0) return AES_E_ARG;
+    const aes_batch_cfg c = cfg ? *cfg : batch_cfg_for(n);
+    return enqueue_batch(desc_dev, n, ws, ws_bytes, status_dev, c, static_cast<cudaStream_t>(stream));
+}
+
+int aes_ecb_batch(const aes_desc *desc_dev, int n, void *stream) {
+    if (n < 0) return AES_E_ARG;
+    if (n == 0) return AES_OK;
+    int dev = 0;
+    if (current_device(&dev) != AES_OK) return AES_E_CUDA;
+    void *ws = nullptr;
+    const size_t need = batch_ws_bytes(n);
+    int st = lib_workspace(dev, need, &ws);
+    if (st != AES_OK) return st;
+    return enqueue_batch(desc_dev, n, ws, need, nullptr, batch_cfg_for(n), static_cast<cudaStream_t>(stream));
+}
+
+int aes_batch_graph_create(const aes_desc *desc_dev, int n, void *ws, size_t ws_bytes, int32_t *status_dev,
+                           const aes_batch_cfg *cfg, aes_batch_graph **out) {
+    if (!out || n <= 0) return AES_E_ARG;
+    *out = nullptr;
+    const aes_batch_cfg c = cfg ? *cfg : batch_cfg_for(n);
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return AES_E_CUDA;
+    BatchGraph *g = new BatchGraph();
+    int st = AES_OK;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = AES_E_CUDA;
+    if (st == AES_OK) {
+        st = enqueue_batch(desc_dev, n, ws, ws_bytes, status_dev, c, s);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(s, &graph);
+        if (st == AES_OK && e != cudaSuccess) st = AES_E_CUDA;
+        g->graph = graph;
+        if (st == AES_OK && cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) st = AES_E_CUDA;
+    }
+    cudaStreamDestroy(s);
+    if (st != AES_OK) {
+        (void)cudaGetLastError();
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        return st;
+    }
+    *out = reinterpret_cast<aes_batch_graph *>(g);
+    return AES_OK;
+}
+
+int aes_batch_graph_launch(aes_batch_graph *graph, void *stream) {
+    if (!graph) return AES_E_ARG;
+    BatchGraph *g = reinterpret_cast<BatchGraph *>(graph);
+    if (cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return AES_E_CUDA;
+    }
+    return AES_OK;
+}
+
+int aes_batch_graph_destroy(aes_batch_graph *graph) {
+    if (!graph) return AES_OK;
+    BatchGraph *g = reinterpret_cast<BatchGraph *>(graph);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return AES_OK;
+}
+
+}  // extern "C"

@@ -6,11 +6,12 @@
 #include <cstdint>
 #include <cstring>
 #include <mutex>
-#include <set>
+#include <map>
 #include <utility>
 
 #include "aesgb.h"
 #include "aes_kernels.cuh"
+#include "batch_internal.h"
 #include "capi_internal.h"
 #include "registry.h"
 
@@ -23,7 +24,7 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::atomic<int> g_sm_count[kMaxDevices];
 std::mutex g_attr_mu;
-std::set<std::pair<const void *, int>> g_attr_done;  // (kernel, device) with smem attribute set
+std::map<std::pair<const void *, int>, uint32_t> g_attr_bytes;  // (kernel, device) -> bytes allowed
 }  // namespace
 
 int current_device(int *dev) {
@@ -42,13 +43,14 @@ int sm_count(int dev) {
 int ensure_smem_attr(const void *fn, int dev, uint32_t bytes) {
     if (bytes <= 48u * 1024u) return AES_OK;
     std::lock_guard<std::mutex> lk(g_attr_mu);
-    if (g_attr_done.count({fn, dev})) return AES_OK;
+    auto it = g_attr_bytes.find({fn, dev});
+    if (it != g_attr_bytes.end() && it->second >= bytes) return AES_OK;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(bytes)) != cudaSuccess) {
         (void)cudaGetLastError();
         return AES_E_CUDA;
     }
-    g_attr_done.insert({fn, dev});
+    g_attr_bytes[{fn, dev}] = bytes;
     return AES_OK;
 }
 
@@ -228,6 +230,7 @@ int aes_host_table(int which, uint32_t *out) {
 
 int aes_shutdown(void) {
     host_io_shutdown();
+    batch_shutdown();
     return AES_OK;
 }
 
