@@ -192,6 +192,24 @@ int aes_ecb_batch_ws(const aes_desc *desc_dev, int n, void *ws, size_t ws_bytes,
  * use aes_ecb_batch_ws with distinct workspaces. */
 int aes_ecb_batch(const aes_desc *desc_dev, int n, void *stream);
 
+/* Batched ECB that allocates nothing: not even the workspace.  The paper has
+ * no counterpart; this exists for callers that must not allocate device
+ * memory -- for example a plugin whose host application hands out only the
+ * buffers it owns, code that runs while another thread is capturing a CUDA
+ * graph in global mode (cudaMalloc is refused then), or a serving thread that
+ * cannot afford cudaMalloc/cudaFree synchronising the whole device.
+ * Same contract and work as aes_ecb_batch_ws, except that the workspace is a
+ * fixed array in the library's device memory (about 330 KB per device that
+ * loads the library, held until the process exits):
+ *   n  at most AES_BATCH_NOALLOC_MAX_DESCS, else AES_E_RANGE (nothing queued).
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call on a device uses the same array, so calls whose work
+ * overlaps on the GPU (different streams without ordering) race and corrupt
+ * each other: order them on one stream or synchronise between them. */
+#define AES_BATCH_NOALLOC_MAX_DESCS 16384
+int aes_ecb_batch_noalloc(const aes_desc *desc_dev, int n, int32_t *status_dev, void *stream);
+
 /* A batch captured once as a CUDA graph (plan + batch kernel) and replayed.
  * desc_dev, ws and status_dev are baked in; the CONTENTS of the descriptor
  * table may change between launches (the plan kernel reads it at run time),

@@ -88,6 +88,7 @@ _SIGNATURES = {
     "aes_batch_workspace_bytes": (_sz, [_i]),
     "aes_ecb_batch_ws": (_i, [_vp, _i, _vp, _sz, _vp, _vp, _vp]),
     "aes_ecb_batch": (_i, [_vp, _i, _vp]),
+    "aes_ecb_batch_noalloc": (_i, [_vp, _i, _vp, _vp]),
     "aes_batch_graph_create": (_i, [_vp, _i, _vp, _sz, _vp, _vp, ctypes.POINTER(_vp)]),
     "aes_batch_graph_launch": (_i, [_vp, _vp]),
     "aes_batch_graph_destroy": (_i, [_vp]),
@@ -263,6 +264,17 @@ def aes_ecb_batch_ws(desc_dev, n: int, ws, ws_bytes: int, status_dev=None, cfg: 
 
 def aes_ecb_batch(desc_dev, n: int, stream=None) -> None:
     _check(lib().aes_ecb_batch(_ptr(desc_dev), int(n), _stream(stream)), "aes_ecb_batch")
+
+
+def aes_ecb_batch_noalloc(desc_dev, n: int, status_dev=None, stream=None) -> None:
+    """Batched ECB with the library's fixed device scratch (no allocation at
+    all); at most AES_BATCH_NOALLOC_MAX_DESCS descriptors, calls must not
+    overlap on the GPU."""
+    _check(lib().aes_ecb_batch_noalloc(_ptr(desc_dev), int(n), _ptr(status_dev), _stream(stream)),
+           "aes_ecb_batch_noalloc")
+
+
+AES_BATCH_NOALLOC_MAX_DESCS = 16384
 
 
 def aes_batch_graph_create(desc_dev, n: int, ws, ws_bytes: int, status_dev=None,

@@ -465,6 +465,41 @@ struct BatchGraph {
     cudaGraphExec_t exec = nullptr;
 };
 
+// ---------------------------------------------------------------------------
+// Batch scratch in a file-scope device array, for callers that cannot
+// allocate device memory (see aes_ecb_batch_noalloc in aesgb.h).
+// ---------------------------------------------------------------------------
+constexpr size_t noalloc_scratch_bytes(size_t n) {
+    return align_up(sizeof(BatchHeader), 256) + align_up(4 * n, 256) + align_up(8 * (n + 1), 256) +
+           align_up(8 * n, 256);
+}
+constexpr size_t kNoAllocBytes = noalloc_scratch_bytes(AES_BATCH_NOALLOC_MAX_DESCS);
+
+// One copy per device that loads this library; it lives until the process exits.
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kMaxDev];  // device address of g_noalloc_scratch, per device
+}  // namespace
+
+// Device address of this device's scratch array, looked up once per device
+// (the host-side name of the array is not a device address).
+int noalloc_scratch_ptr(int dev, void **out) {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            (void)cudaGetLastError();
+            return AES_E_CUDA;
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return AES_OK;
+}
+
 }  // namespace aesgb
 
 using namespace aesgb;
@@ -490,6 +525,23 @@ int aes_ecb_batch(const aes_desc *desc_dev, int n, void *stream) {
     int st = lib_workspace(dev, need, &ws);
     if (st != AES_OK) return st;
     return enqueue_batch(desc_dev, n, ws, need, nullptr, batch_cfg_for(n), static_cast<cudaStream_t>(stream));
+}
+
+int aes_ecb_batch_noalloc(const aes_desc *desc_dev, int n, int32_t *status_dev, void *stream) {
+    if (n < 0) return AES_E_ARG;
+    if (n > AES_BATCH_NOALLOC_MAX_DESCS) return AES_E_RANGE;
+    if (n == 0) return AES_OK;
+    if (batch_ws_bytes(n) > kNoAllocBytes) return AES_E_RANGE;
+    int dev = 0;
+    if (current_device(&dev) != AES_OK) return AES_E_CUDA;
+    void *scratch = nullptr;
+    const int st = noalloc_scratch_ptr(dev, &scratch);
+    if (st != AES_OK) return st;
+    // the plan kernel rewrites the header (work counters zeroed) and every
+    // array the batch kernel reads, so what the previous call left behind in
+    // the scratch is never used
+    return enqueue_batch(desc_dev, n, scratch, kNoAllocBytes, status_dev, batch_cfg_for(n),
+                         static_cast<cudaStream_t>(stream));
 }
 
 int aes_batch_graph_create(const aes_desc *desc_dev, int n, void *ws, size_t ws_bytes, int32_t *status_dev,
