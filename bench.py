@@ -58,6 +58,9 @@ def parse_args():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-sweep", action="store_true")
     p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--no-served", action="store_true")
+    p.add_argument("--no-tune", action="store_true")
+    p.add_argument("--served-requests", type=int, default=20000)
     return p.parse_args()
 
 
@@ -320,7 +323,7 @@ def run_sweep(torch, aesgb, dev):
     return rows
 
 
-def run_batched(torch, aesgb, dev, n=4096):
+def run_batched(torch, aesgb, dev, n=4096, tune=True):
     """Batched workload: 4,096 messages, log-uniform 16 B .. 16 MiB, key size
     uniform over {128,192,256}, direction 50/50 -- one persistent launch from a
     device descriptor table replayed as a CUDA graph, against the same messages
@@ -367,6 +370,7 @@ def run_batched(torch, aesgb, dev, n=4096):
         e_.synchronize()
         return s_.elapsed_time(e_) / iters
 
+    tuned = repr(aesgb.aes_tune_batch(desc, n, ws, ws_bytes, stream)) if tune else None
     graph = aesgb.aes_batch_graph_create(desc, n, ws, ws_bytes)
     try:
         for _ in range(2):
@@ -419,8 +423,78 @@ def run_batched(torch, aesgb, dev, n=4096):
            "loop_python_ms": round(ms_loop_py, 3), "loop_python_gbps": round(gb / (ms_loop_py / 1e3), 1),
            "speedup_vs_loop_graph": round(ms_loop_graph / ms_batch, 3),
            "speedup_vs_loop_python": round(ms_loop_py / ms_batch, 3),
-           "identical_to_loop": same, "cfg": repr(aesgb.make_batch_cfg())}
+           "identical_to_loop": same, "cfg": repr(aesgb.aes_batch_get_cfg(n)), "tuned": tuned is not None}
     del src, dst, ref, rk_dev, desc, ws
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_served(torch, aesgb, dev, n_req=20000, loads=(0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9, 1.0)):
+    """Served workload: a Poisson stream of encrypt/decrypt requests, sizes
+    log-uniform 64 B .. 4 MiB, keys drawn from 1,024 resident schedules,
+    direction 50/50, through the continuous-batching server under a 4 GiB
+    device-memory budget.  Peak = the same requests all arriving at once;
+    offered load is then swept as a fraction of that peak."""
+    import numpy as np
+    from paper_1902_05234_gb300 import workloads as wl
+    unit_arrivals, sizes, key_ids, dirs = wl.served_workload(n_req, rate_per_s=1.0, n_keys=1024)
+    offs = np.zeros(n_req + 1, np.int64)
+    np.cumsum(sizes, out=offs[1:])
+    total = int(offs[-1])
+    src = torch.empty(total, dtype=torch.uint8, device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(wl.BASE_SEED + 60)
+    src.random_(0, 256, generator=g)
+    dst = torch.empty_like(src)
+    ins = src.data_ptr() + offs[:-1].astype(np.uint64)
+    outs = dst.data_ptr() + offs[:-1].astype(np.uint64)
+    srv = aesgb.aes_srv_create(4 << 30, 1024, max_batch=8192, slots=4)
+    try:
+        kg = wl.rng(61)
+        for k in range(1024):
+            kb = int(kg.choice([128, 192, 256]))
+            aesgb.aes_srv_put_key(srv, k, kb, kg.integers(0, 256, kb // 8, dtype=np.uint8).tobytes())
+
+        def run(offsets):
+            st, tickets = aesgb.aes_srv_submit_many(srv, key_ids, dirs, ins, outs, sizes, offsets)
+            if st != 0:
+                raise SystemExit(f"served: submission refused ({st})")
+            aesgb.aes_srv_drain(srv, 600000)
+            status, lat, queue = aesgb.aes_srv_results(srv, tickets, release=True)
+            if not np.all(status == 0):
+                raise SystemExit("served: a request failed")
+            arr = offsets if offsets is not None else np.zeros(n_req)
+            span = float(np.max(arr + lat) - np.min(arr))
+            return lat, queue, span
+
+        run(None)                                   # warm-up (tuned configuration, first launches)
+        ref = dst.clone()
+        lat, _, span = run(None)                    # saturated: every request at once
+        peak_bps = total / span
+        rows = []
+        identical = bool(torch.equal(dst, ref))
+        mean_size = float(np.mean(sizes))
+        for load in loads:
+            rate = load * peak_bps / mean_size
+            offsets = unit_arrivals / rate
+            offsets = offsets - offsets[0]
+            lat, queue, span = run(offsets)
+            identical = identical and bool(torch.equal(dst, ref))
+            rows.append({"load": load, "offered_gbps": round(load * peak_bps * 8 / 1e9, 1),
+                         "gbps": round(total * 8 / span / 1e9, 1),
+                         "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 4),
+                         "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 4),
+                         "p99_queue_ms": round(float(np.percentile(queue, 99)) * 1e3, 4)})
+        stats = aesgb.aes_srv_stats(srv)
+    finally:
+        aesgb.aes_srv_destroy(srv)
+    out = {"workload": f"{n_req} requests per load point, Poisson arrivals, sizes log-uniform 64 B..4 MiB "
+                       f"(total {total:,} B), 1,024 resident keys (128/192/256), direction 50/50, "
+                       f"4 GiB budget, 4 in-flight batches",
+           "peak_gbps": round(peak_bps * 8 / 1e9, 1), "sweep": rows,
+           "identical_across_loads": identical, "batches_total": stats["batches"],
+           "peak_inflight_bytes": stats["peak_inflight_bytes"]}
+    del src, dst, ref
     torch.cuda.empty_cache()
     return out
 
@@ -455,6 +529,13 @@ def run_gb300(args, dist: Dist):
         if ev is not None:
             ev[2][k].record(stream)
 
+    tuned = None
+    if not args.no_tune:
+        # the autotuner picks block size, bytes per thread and table layout for
+        # this size, untimed; aes_ecb_encrypt/decrypt then use its choice
+        enc0, dec0, nr0 = aesgb.aes_expand_key(args.keybits, key)
+        tuned = {"enc": repr(aesgb.aes_tune_ecb(0, nr0, enc0, pt, ct, nblocks)),
+                 "dec": repr(aesgb.aes_tune_ecb(1, nr0, dec0, pt, back, nblocks))}
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
@@ -530,13 +611,16 @@ def run_gb300(args, dist: Dist):
             "enc_gbps": round(enc_gbps, 1), "dec_gbps": round(dec_gbps, 1),
             "roofline": roofline, "e2e": e2e, "gpu_launches": 2 * K * world,
             "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")} | {"samples": clk["samples"]},
-            "launch_cfg": repr(aesgb.aes_ecb_get_cfg(0, nr, nblocks))}
+            "launch_cfg": {"enc": repr(aesgb.aes_ecb_get_cfg(0, nr, nblocks)),
+                           "dec": repr(aesgb.aes_ecb_get_cfg(1, nr, nblocks)), "tuned": tuned is not None}}
     del ct, back
     torch.cuda.empty_cache()
     if dist.rank == 0 and world == 1 and not args.no_sweep:
         line["sweep"] = run_sweep(torch, aesgb, dev)
     if dist.rank == 0 and world == 1 and not args.no_batched:
-        line["batched"] = run_batched(torch, aesgb, dev)
+        line["batched"] = run_batched(torch, aesgb, dev, tune=not args.no_tune)
+    if dist.rank == 0 and world == 1 and not args.no_served:
+        line["served"] = run_served(torch, aesgb, dev, n_req=args.served_requests)
     if dist.rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.keybits)
     if dist.rank == 0:

@@ -247,6 +247,112 @@ int aes_ecb_host(int dir, const uint32_t *rk, int nrounds, const uint8_t *host_i
 int aes_shutdown(void);
 
 /* ------------------------------------------------------------------------ */
+/* Serving: continuous batching over the batch kernel                        */
+/* ------------------------------------------------------------------------ */
+/* A request is ECB (eq (1)) of one caller-owned device buffer with a
+ * resident key.  The server's dispatcher thread admits requests in arrival
+ * order while the bytes in flight (2 x nbytes per admitted, unfinished
+ * request: input and output) stay within mem_budget_bytes, packs everything
+ * admitted into one batch whenever one of `slots` in-flight batch slots is
+ * free, and launches it on that slot's stream (descriptor upload, the plan and
+ * persistent batch kernels, status download, completion event).  Requests
+ * that arrive while earlier batches run join the next batch; consecutive
+ * batches overlap on the device.  Host waits are bounded; nothing waits on the
+ * device.  Latency = host arrival -> host-observed completion.
+ * A server handle is used from one host thread at a time (plus its own
+ * dispatcher); it works on the device that was current at creation. */
+typedef struct aes_server aes_server;
+
+typedef struct aes_srv_stats_t {
+    uint64_t submitted, completed, batches, bytes_completed;
+    uint64_t inflight_bytes, peak_inflight_bytes, pending;
+    double busy_s;          /* first arrival -> last completion            */
+    int32_t worker_status;  /* AES_OK, or the first dispatcher CUDA error   */
+    int32_t reserved;
+} aes_srv_stats_t;
+
+/* Create a server: key store for max_keys expanded schedules (device),
+ * `slots` in-flight batches (1..16), at most max_batch requests per batch.
+ * Allocates its device and page-locked memory here (AES_E_NOMEM). */
+int aes_srv_create(size_t mem_budget_bytes, int max_keys, int max_batch, int slots, aes_server **srv);
+
+/* Expand key (HOST, keybits/8 bytes) and keep both schedules resident under
+ * key_id (0..max_keys-1); synchronous.  Replace a key only while no request
+ * using it is in flight. */
+int aes_srv_put_key(aes_server *srv, int key_id, int keybits, const uint8_t *key);
+
+/* Submit one request arriving now: in_dev/out_dev DEVICE, 16-byte aligned,
+ * equal or disjoint, nbytes a multiple of 16 with 2*nbytes <= budget
+ * (AES_E_RANGE), key_id resident (AES_E_NOTFOUND).  *ticket identifies it. */
+int aes_srv_submit(aes_server *srv, int key_id, int dir, const uint8_t *in_dev, uint8_t *out_dev,
+                   size_t nbytes, uint64_t *ticket);
+
+/* Submit n requests whose arrival times are now + arrival_offsets_s[i]
+ * (seconds, non-decreasing; NULL = all now) -- an open-loop request stream
+ * replayed by the server.  Arrays are HOST; device addresses as uint64.
+ * tickets[i] = 0 for a rejected request; returns the first rejection status. */
+int aes_srv_submit_many(aes_server *srv, int n, const int32_t *key_ids, const int32_t *dirs,
+                        const uint64_t *in_devs, const uint64_t *out_devs, const uint64_t *nbytes,
+                        const double *arrival_offsets_s, uint64_t *tickets);
+
+/* Non-blocking check: *done = 1 once finished; then *status (per-request
+ * aes_status) and *latency_s (may be NULL). */
+int aes_srv_poll(aes_server *srv, uint64_t ticket, int *done, int *status, double *latency_s);
+
+/* Block up to timeout_ms for one request (AES_E_TIMEOUT), or for all (drain). */
+int aes_srv_wait(aes_server *srv, uint64_t ticket, int timeout_ms, int *status, double *latency_s);
+int aes_srv_drain(aes_server *srv, int timeout_ms);
+
+/* Statuses, latencies and queueing delays (arrival -> admission) of n
+ * finished requests (HOST arrays, any may be NULL except tickets); release != 0
+ * forgets them afterwards.  AES_E_BUSY if some are not finished. */
+int aes_srv_results(aes_server *srv, int n, const uint64_t *tickets, int32_t *status, double *latency_s,
+                    double *queue_s, int release);
+
+int aes_srv_stats(aes_server *srv, aes_srv_stats_t *out);
+
+/* Stop the dispatcher (requests not yet launched are dropped), wait for the
+ * batches in flight and free everything. */
+int aes_srv_destroy(aes_server *srv);
+
+/* ------------------------------------------------------------------------ */
+/* Autotuner                                                                 */
+/* ------------------------------------------------------------------------ */
+/* The granularity (16, 32 or 64 bytes per thread: the axis of the paper's
+ * related work, section 2) and the table placement (section 4.2) are chosen
+ * per GPU by timing.  Tuned entries are kept per (SM count, direction,
+ * nrounds, size class = floor(log4(nblocks))) for the single-buffer calls and
+ * per SM count for batches; aes_ecb_encrypt/decrypt and the batch calls use
+ * them from then on.  If the environment variable AESGB_TUNE_CACHE names a
+ * file, entries are loaded from it on first use and written to it after each
+ * tuning run.  Tuning launches the kernels many times on the given buffers
+ * (out is overwritten, in is only read), synchronises `stream` and takes
+ * seconds. */
+
+/* Tune the single-buffer kernel for (dir, nrounds, size class of nblocks) on
+ * the caller's DEVICE buffers (same rules as aes_ecb_crypt_cfg; rk HOST).
+ * best (HOST, may be NULL) receives the chosen configuration. */
+int aes_tune_ecb(int dir, int nrounds, const uint32_t *rk, const uint8_t *in, uint8_t *out, size_t nblocks,
+                 void *stream, aes_launch_cfg *best);
+
+/* Tune the batch kernel on a caller's batch (same arguments as
+ * aes_ecb_batch_ws without status; the batch is run many times). */
+int aes_tune_batch(const aes_desc *desc_dev, int n, void *ws, size_t ws_bytes, void *stream,
+                   aes_batch_cfg *best);
+
+/* Record a configuration by hand for (dir, nrounds, size class of nblocks). */
+int aes_tune_set_ecb(int dir, int nrounds, size_t nblocks, const aes_launch_cfg *cfg);
+
+/* The configuration the batch calls would use for n descriptors. */
+int aes_batch_get_cfg(int n, aes_batch_cfg *cfg);
+
+/* Write / read the tuned entries to / from a text file (path HOST); clear all
+ * entries (the defaults apply again). */
+int aes_tune_save(const char *path);
+int aes_tune_load(const char *path);
+int aes_tune_clear(void);
+
+/* ------------------------------------------------------------------------ */
 /* Introspection                                                             */
 /* ------------------------------------------------------------------------ */
 

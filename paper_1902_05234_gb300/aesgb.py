@@ -62,6 +62,16 @@ class aes_batch_cfg(ctypes.Structure):
                 f"chunk_passes={self.chunk_passes}, ctas_per_sm={self.ctas_per_sm})")
 
 
+class aes_srv_stats_t(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("bytes_completed", ctypes.c_uint64), ("inflight_bytes", ctypes.c_uint64),
+                ("peak_inflight_bytes", ctypes.c_uint64), ("pending", ctypes.c_uint64),
+                ("busy_s", ctypes.c_double), ("worker_status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
 # numpy view of aes_desc (40 bytes) for building descriptor tables in bulk
 DESC_DTYPE = np.dtype([("rk", "<u8"), ("in", "<u8"), ("out", "<u8"), ("nblocks", "<u8"),
                        ("nrounds", "<i4"), ("dir", "<i4")])
@@ -93,6 +103,24 @@ _SIGNATURES = {
     "aes_batch_graph_launch": (_i, [_vp, _vp]),
     "aes_batch_graph_destroy": (_i, [_vp]),
     "aes_shutdown": (_i, []),
+    "aes_tune_ecb": (_i, [_i, _i, _u32p, _vp, _vp, _sz, _vp, ctypes.POINTER(aes_launch_cfg)]),
+    "aes_tune_batch": (_i, [_vp, _i, _vp, _sz, _vp, ctypes.POINTER(aes_batch_cfg)]),
+    "aes_tune_set_ecb": (_i, [_i, _i, _sz, ctypes.POINTER(aes_launch_cfg)]),
+    "aes_batch_get_cfg": (_i, [_i, ctypes.POINTER(aes_batch_cfg)]),
+    "aes_tune_save": (_i, [ctypes.c_char_p]),
+    "aes_tune_load": (_i, [ctypes.c_char_p]),
+    "aes_tune_clear": (_i, []),
+    "aes_srv_create": (_i, [_sz, _i, _i, _i, ctypes.POINTER(_vp)]),
+    "aes_srv_put_key": (_i, [_vp, _i, _i, _u8p]),
+    "aes_srv_submit": (_i, [_vp, _i, _i, _vp, _vp, _sz, ctypes.POINTER(ctypes.c_uint64)]),
+    "aes_srv_submit_many": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "aes_srv_poll": (_i, [_vp, ctypes.c_uint64, ctypes.POINTER(_i), ctypes.POINTER(_i),
+                          ctypes.POINTER(ctypes.c_double)]),
+    "aes_srv_wait": (_i, [_vp, ctypes.c_uint64, _i, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_double)]),
+    "aes_srv_drain": (_i, [_vp, _i]),
+    "aes_srv_results": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _i]),
+    "aes_srv_stats": (_i, [_vp, ctypes.POINTER(aes_srv_stats_t)]),
+    "aes_srv_destroy": (_i, [_vp]),
     "aes_device_table": (_i, [_i, _u32p]),
 }
 
@@ -245,6 +273,121 @@ def aes_ecb_host(direction: int, rk, nrounds: int, host_in, host_out, nblocks: i
     p, _keep = _rk_arg(rk)
     _check(lib().aes_ecb_host(int(direction), p, int(nrounds), _ptr(host_in), _ptr(host_out), int(nblocks),
                               _ptr(dev_buf), int(dev_buf_bytes), _stream(stream)), "aes_ecb_host")
+
+
+def aes_tune_ecb(direction: int, nrounds: int, rk, in_, out, nblocks: int, stream=None) -> aes_launch_cfg:
+    p, _keep = _rk_arg(rk)
+    c = aes_launch_cfg()
+    _check(lib().aes_tune_ecb(int(direction), int(nrounds), p, _ptr(in_), _ptr(out), int(nblocks),
+                              _stream(stream), ctypes.byref(c)), "aes_tune_ecb")
+    return c
+
+
+def aes_tune_batch(desc_dev, n: int, ws, ws_bytes: int, stream=None) -> aes_batch_cfg:
+    c = aes_batch_cfg()
+    _check(lib().aes_tune_batch(_ptr(desc_dev), int(n), _ptr(ws), int(ws_bytes), _stream(stream),
+                                ctypes.byref(c)), "aes_tune_batch")
+    return c
+
+
+def aes_tune_set_ecb(direction: int, nrounds: int, nblocks: int, cfg: aes_launch_cfg) -> None:
+    _check(lib().aes_tune_set_ecb(int(direction), int(nrounds), int(nblocks), ctypes.byref(cfg)),
+           "aes_tune_set_ecb")
+
+
+def aes_batch_get_cfg(n: int) -> aes_batch_cfg:
+    c = aes_batch_cfg()
+    _check(lib().aes_batch_get_cfg(int(n), ctypes.byref(c)), "aes_batch_get_cfg")
+    return c
+
+
+def aes_tune_save(path: str) -> None:
+    _check(lib().aes_tune_save(os.fsencode(path)), "aes_tune_save")
+
+
+def aes_tune_load(path: str) -> None:
+    _check(lib().aes_tune_load(os.fsencode(path)), "aes_tune_load")
+
+
+def aes_tune_clear() -> None:
+    _check(lib().aes_tune_clear(), "aes_tune_clear")
+
+
+# --- serving ----------------------------------------------------------------
+
+def aes_srv_create(mem_budget_bytes: int, max_keys: int, max_batch: int = 4096, slots: int = 3) -> int:
+    h = _vp()
+    _check(lib().aes_srv_create(int(mem_budget_bytes), int(max_keys), int(max_batch), int(slots),
+                                ctypes.byref(h)), "aes_srv_create")
+    return int(h.value)
+
+
+def aes_srv_put_key(srv: int, key_id: int, keybits: int, key) -> None:
+    k = np.ascontiguousarray(np.frombuffer(bytes(key), np.uint8))
+    _check(lib().aes_srv_put_key(_vp(srv), int(key_id), int(keybits), k.ctypes.data_as(_u8p)),
+           "aes_srv_put_key")
+
+
+def aes_srv_submit(srv: int, key_id: int, direction: int, in_dev, out_dev, nbytes: int) -> int:
+    t = ctypes.c_uint64()
+    _check(lib().aes_srv_submit(_vp(srv), int(key_id), int(direction), _ptr(in_dev), _ptr(out_dev),
+                                int(nbytes), ctypes.byref(t)), "aes_srv_submit")
+    return int(t.value)
+
+
+def aes_srv_submit_many(srv: int, key_ids, dirs, in_devs, out_devs, nbytes, arrival_offsets_s=None):
+    """Returns (status, tickets uint64[n])."""
+    n = len(nbytes)
+    k = np.ascontiguousarray(key_ids, np.int32)
+    d = np.ascontiguousarray(dirs, np.int32)
+    i = np.ascontiguousarray(in_devs, np.uint64)
+    o = np.ascontiguousarray(out_devs, np.uint64)
+    b = np.ascontiguousarray(nbytes, np.uint64)
+    a = None if arrival_offsets_s is None else np.ascontiguousarray(arrival_offsets_s, np.float64)
+    t = np.zeros(n, np.uint64)
+    st = lib().aes_srv_submit_many(_vp(srv), n, k.ctypes.data, d.ctypes.data, i.ctypes.data, o.ctypes.data,
+                                   b.ctypes.data, None if a is None else a.ctypes.data, t.ctypes.data)
+    return int(st), t
+
+
+def aes_srv_poll(srv: int, ticket: int):
+    done, st, lat = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(lib().aes_srv_poll(_vp(srv), int(ticket), ctypes.byref(done), ctypes.byref(st), ctypes.byref(lat)),
+           "aes_srv_poll")
+    return bool(done.value), int(st.value), float(lat.value)
+
+
+def aes_srv_wait(srv: int, ticket: int, timeout_ms: int = 10000):
+    st, lat = ctypes.c_int(), ctypes.c_double()
+    _check(lib().aes_srv_wait(_vp(srv), int(ticket), int(timeout_ms), ctypes.byref(st), ctypes.byref(lat)),
+           "aes_srv_wait")
+    return int(st.value), float(lat.value)
+
+
+def aes_srv_drain(srv: int, timeout_ms: int = 60000) -> None:
+    _check(lib().aes_srv_drain(_vp(srv), int(timeout_ms)), "aes_srv_drain")
+
+
+def aes_srv_results(srv: int, tickets, release: bool = False):
+    """Returns (status int32[n], latency_s float64[n], queue_s float64[n])."""
+    t = np.ascontiguousarray(tickets, np.uint64)
+    n = t.size
+    st = np.zeros(n, np.int32)
+    lat = np.zeros(n, np.float64)
+    q = np.zeros(n, np.float64)
+    _check(lib().aes_srv_results(_vp(srv), n, t.ctypes.data, st.ctypes.data, lat.ctypes.data, q.ctypes.data,
+                                 int(bool(release))), "aes_srv_results")
+    return st, lat, q
+
+
+def aes_srv_stats(srv: int) -> dict:
+    s = aes_srv_stats_t()
+    _check(lib().aes_srv_stats(_vp(srv), ctypes.byref(s)), "aes_srv_stats")
+    return s.as_dict()
+
+
+def aes_srv_destroy(srv: int) -> None:
+    _check(lib().aes_srv_destroy(_vp(srv)), "aes_srv_destroy")
 
 
 def aes_shutdown() -> None:

@@ -1,0 +1,463 @@
+// serve.cpp -- continuous-batching ECB request server (aes_srv_*).
+//
+// Requests name a resident key (expanded once with aes_expand_key and kept in
+// device memory), a direction and caller-owned device buffers.  A dispatcher
+// thread owned by the server:
+//   * admits requests in arrival order while the bytes in flight (input +
+//     output of every admitted, unfinished request) stay within the budget;
+//     a request that does not fit waits, and so do the ones behind it (FIFO);
+//   * packs every admitted request into one batch as soon as one of the
+//     in-flight slots is free, and launches it (descriptor upload, plan and
+//     persistent batch kernels, status download, completion event) on that
+//     slot's stream -- so requests that arrive while earlier batches run are
+//     admitted as slots and budget free up, and consecutive batches overlap
+//     on the device;
+//   * retires a slot when its event has completed: the requests' statuses and
+//     completion times are recorded and their bytes leave the budget.
+// Host waits are bounded (condition variables with timeouts); nothing on the
+// device waits.  Latency is host arrival -> host-observed completion.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdint>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "batch_internal.h"
+#include "capi_internal.h"
+
+namespace aesgb {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double now_s() {
+    return std::chrono::duration<double>(Clock::now().time_since_epoch()).count();
+}
+
+struct Req {
+    int key_id = 0, dir = 0;
+    const uint8_t *in = nullptr;
+    uint8_t *out = nullptr;
+    size_t nbytes = 0;
+    double arrival = 0, admitted = 0, done_t = 0;
+    int status = 0;
+    bool done = false;
+    bool released = false;
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    aes_desc *h_desc = nullptr;
+    aes_desc *d_desc = nullptr;
+    int32_t *h_status = nullptr;
+    int32_t *d_status = nullptr;
+    void *d_ws = nullptr;
+    size_t ws_bytes = 0;
+    bool busy = false;
+    size_t bytes = 0;
+    std::vector<uint64_t> tickets;
+};
+
+struct Server {
+    int dev = 0;
+    size_t budget = 0, inflight = 0, peak_inflight = 0;
+    int max_keys = 0, max_batch = 0;
+    uint32_t *d_rk_enc = nullptr, *d_rk_dec = nullptr;  // max_keys x 64 words
+    std::vector<int> key_nr;
+    std::vector<Slot> slots;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<uint64_t> pending;
+    // requests by ticket: tickets are consecutive, reqs[t - base] is ticket t;
+    // released requests are dropped from the front
+    std::deque<Req> reqs;
+    uint64_t base = 1;
+    Req *find(uint64_t t) { return t >= base && t - base < reqs.size() ? &reqs[t - base] : nullptr; }
+    std::thread worker;
+    bool stop = false;
+    int worker_error = AES_OK;
+    // statistics
+    uint64_t n_submitted = 0, n_completed = 0, n_batches = 0, bytes_completed = 0;
+    double first_arrival = 0, last_done = 0;
+};
+
+constexpr uint32_t kRkStrideWords = 64;
+
+void free_server(Server *s) {
+    for (Slot &sl : s->slots) {
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
+        if (sl.ev) cudaEventDestroy(sl.ev);
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+        if (sl.h_desc) cudaFreeHost(sl.h_desc);
+        if (sl.h_status) cudaFreeHost(sl.h_status);
+        if (sl.d_desc) cudaFree(sl.d_desc);
+        if (sl.d_status) cudaFree(sl.d_status);
+        if (sl.d_ws) cudaFree(sl.d_ws);
+    }
+    if (s->d_rk_enc) cudaFree(s->d_rk_enc);
+    if (s->d_rk_dec) cudaFree(s->d_rk_dec);
+    delete s;
+}
+
+// Batch configuration for a batch of `total_blocks`: chunks small enough that
+// every warp of the grid gets several (latency at light load), at most the
+// throughput-tuned chunk size.
+aes_batch_cfg serve_cfg(int sms, unsigned long long total_blocks) {
+    aes_batch_cfg c = batch_cfg_for(0);
+    const unsigned long long warps = static_cast<unsigned long long>(sms) * (c.threads / 32);
+    const unsigned long long per_pass = 32ull * c.blocks_per_thread;
+    unsigned long long passes = total_blocks / (warps * 4 * per_pass);
+    if (passes < 1) passes = 1;
+    if (passes > static_cast<unsigned long long>(c.chunk_passes)) passes = c.chunk_passes;
+    c.chunk_passes = static_cast<int32_t>(passes);
+    return c;
+}
+
+// Retire finished slots (mu held).
+void retire_locked(Server *s) {
+    for (Slot &sl : s->slots) {
+        if (!sl.busy) continue;
+        const cudaError_t q = cudaEventQuery(sl.ev);
+        if (q == cudaErrorNotReady) continue;
+        const double t = now_s();
+        const bool ok = q == cudaSuccess;
+        if (!ok) (void)cudaGetLastError();
+        for (size_t i = 0; i < sl.tickets.size(); ++i) {
+            Req *rp = s->find(sl.tickets[i]);
+            if (!rp) continue;
+            Req &r = *rp;
+            r.done = true;
+            r.done_t = t;
+            r.status = ok ? sl.h_status[i] : AES_E_CUDA;
+            s->n_completed++;
+            s->bytes_completed += r.nbytes;
+            s->last_done = t;
+        }
+        s->inflight -= sl.bytes;
+        sl.bytes = 0;
+        sl.tickets.clear();
+        sl.busy = false;
+    }
+}
+
+// Admit and launch one batch on a free slot (mu held).  Returns true if a
+// batch was launched.
+bool dispatch_locked(Server *s, int sms) {
+    Slot *sl = nullptr;
+    for (Slot &x : s->slots)
+        if (!x.busy) { sl = &x; break; }
+    if (!sl || s->pending.empty()) return false;
+    const double t = now_s();
+    int n = 0;
+    size_t bytes = 0;
+    unsigned long long blocks = 0;
+    while (!s->pending.empty() && n < s->max_batch) {
+        Req &r = *s->find(s->pending.front());
+        if (r.arrival > t) break;                          // not arrived yet
+        const size_t need = 2 * r.nbytes;
+        if (s->inflight + bytes + need > s->budget) break;  // FIFO: wait for budget
+        const int nr = s->key_nr[r.key_id];
+        aes_desc &d = sl->h_desc[n];
+        d.rk = (r.dir == 0 ? s->d_rk_enc : s->d_rk_dec) + static_cast<size_t>(r.key_id) * kRkStrideWords;
+        d.in = r.in;
+        d.out = r.out;
+        d.nblocks = r.nbytes / 16;
+        d.nrounds = nr;
+        d.dir = r.dir;
+        r.admitted = t;
+        sl->tickets.push_back(s->pending.front());
+        s->pending.pop_front();
+        bytes += need;
+        blocks += d.nblocks;
+        ++n;
+    }
+    if (n == 0) return false;
+    const aes_batch_cfg cfg = serve_cfg(sms, blocks);
+    bool ok = cudaMemcpyAsync(sl->d_desc, sl->h_desc, sizeof(aes_desc) * n, cudaMemcpyHostToDevice,
+                              sl->stream) == cudaSuccess;
+    ok = ok && aes_ecb_batch_ws(sl->d_desc, n, sl->d_ws, sl->ws_bytes, sl->d_status, &cfg, sl->stream) == AES_OK;
+    ok = ok && cudaMemcpyAsync(sl->h_status, sl->d_status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost,
+                               sl->stream) == cudaSuccess;
+    ok = ok && cudaEventRecord(sl->ev, sl->stream) == cudaSuccess;
+    if (!ok) {
+        (void)cudaGetLastError();
+        s->worker_error = AES_E_CUDA;
+        for (int i = 0; i < n; ++i) sl->h_status[i] = AES_E_CUDA;
+        // the event may not have been recorded: mark the batch done now
+        for (size_t i = 0; i < sl->tickets.size(); ++i) {
+            Req &r = *s->find(sl->tickets[i]);
+            r.done = true;
+            r.done_t = now_s();
+            r.status = AES_E_CUDA;
+            s->n_completed++;
+        }
+        sl->tickets.clear();
+        return true;
+    }
+    sl->busy = true;
+    sl->bytes = bytes;
+    s->inflight += bytes;
+    s->peak_inflight = std::max(s->peak_inflight, s->inflight);
+    s->n_batches++;
+    return true;
+}
+
+void worker_main(Server *s) {
+    cudaSetDevice(s->dev);
+    const int sms = sm_count(s->dev) > 0 ? sm_count(s->dev) : 1;
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (!s->stop) {
+        const uint64_t before = s->n_completed;
+        retire_locked(s);
+        bool launched = false;
+        while (dispatch_locked(s, sms)) launched = true;
+        if (s->n_completed != before) s->cv_done.notify_all();
+        bool any_busy = false;
+        for (const Slot &sl : s->slots) any_busy |= sl.busy;
+        if (launched) continue;
+        if (any_busy) {
+            // poll the slots' events again shortly (host side, bounded)
+            s->cv_work.wait_for(lk, std::chrono::microseconds(20));
+        } else if (!s->pending.empty()) {
+            const double wait = s->find(s->pending.front())->arrival - now_s();
+            if (wait > 0)
+                s->cv_work.wait_for(lk, std::chrono::duration<double>(std::min(wait, 0.01)));
+        } else {
+            s->cv_work.wait_for(lk, std::chrono::milliseconds(10));
+        }
+    }
+}
+
+}  // namespace
+}  // namespace aesgb
+
+using namespace aesgb;
+
+struct aes_server {};  // opaque handle type of the C ABI (aesgb::Server behind it)
+
+static Server *as_server(aes_server *h) { return reinterpret_cast<Server *>(h); }
+
+extern "C" {
+
+int aes_srv_create(size_t mem_budget_bytes, int max_keys, int max_batch, int slots, aes_server **out) {
+    if (!out || mem_budget_bytes < 32 || max_keys <= 0 || max_batch <= 0 || slots <= 0 || slots > 16)
+        return AES_E_ARG;
+    *out = nullptr;
+    Server *s = new Server();
+    s->budget = mem_budget_bytes;
+    s->max_keys = max_keys;
+    s->max_batch = max_batch;
+    s->key_nr.assign(static_cast<size_t>(max_keys), -1);
+    int st = current_device(&s->dev);
+    const size_t rk_bytes = static_cast<size_t>(max_keys) * kRkStrideWords * 4;
+    bool ok = st == AES_OK && cudaMalloc(&s->d_rk_enc, rk_bytes) == cudaSuccess &&
+              cudaMalloc(&s->d_rk_dec, rk_bytes) == cudaSuccess;
+    s->slots.resize(static_cast<size_t>(slots));
+    for (Slot &sl : s->slots) {
+        if (!ok) break;
+        sl.ws_bytes = aes_batch_workspace_bytes(max_batch);
+        ok = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) == cudaSuccess &&
+             cudaMallocHost(&sl.h_desc, sizeof(aes_desc) * max_batch) == cudaSuccess &&
+             cudaMallocHost(&sl.h_status, sizeof(int32_t) * max_batch) == cudaSuccess &&
+             cudaMalloc(&sl.d_desc, sizeof(aes_desc) * max_batch) == cudaSuccess &&
+             cudaMalloc(&sl.d_status, sizeof(int32_t) * max_batch) == cudaSuccess &&
+             cudaMalloc(&sl.d_ws, sl.ws_bytes) == cudaSuccess;
+        sl.tickets.reserve(static_cast<size_t>(max_batch));
+    }
+    if (!ok) {
+        (void)cudaGetLastError();
+        free_server(s);
+        return st == AES_OK ? AES_E_NOMEM : st;
+    }
+    s->worker = std::thread(worker_main, s);
+    *out = reinterpret_cast<aes_server *>(s);
+    return AES_OK;
+}
+
+int aes_srv_put_key(aes_server *h, int key_id, int keybits, const uint8_t *key) {
+    Server *s = as_server(h);
+    if (!s || key_id < 0 || key_id >= s->max_keys) return AES_E_ARG;
+    uint32_t enc[kRkStrideWords] = {0}, dec[kRkStrideWords] = {0};
+    const int nr = expand_key_host(keybits, key, enc, dec);
+    if (nr < 0) return nr;
+    const size_t off = static_cast<size_t>(key_id) * kRkStrideWords;
+    std::lock_guard<std::mutex> lk(s->mu);
+    cudaSetDevice(s->dev);
+    if (cudaMemcpy(s->d_rk_enc + off, enc, sizeof enc, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(s->d_rk_dec + off, dec, sizeof dec, cudaMemcpyHostToDevice) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return AES_E_CUDA;
+    }
+    s->key_nr[key_id] = nr;
+    return AES_OK;
+}
+
+static int submit_locked(Server *s, int key_id, int dir, const uint8_t *in, uint8_t *out, size_t nbytes,
+                         double arrival, uint64_t *ticket) {
+    if (key_id < 0 || key_id >= s->max_keys) return AES_E_NOTFOUND;
+    if (s->key_nr[key_id] < 0) return AES_E_NOTFOUND;
+    if (dir != 0 && dir != 1) return AES_E_ARG;
+    if (nbytes % 16) return AES_E_ARG;
+    if (2 * nbytes > s->budget) return AES_E_RANGE;
+    if (nbytes && (!in || !out)) return AES_E_ARG;
+    const int st = check_buffers(in ? in : reinterpret_cast<const uint8_t *>(16),
+                                 out ? out : reinterpret_cast<uint8_t *>(16), nbytes / 16);
+    if (nbytes && st != AES_OK) return st;
+    const uint64_t t = s->base + s->reqs.size();
+    Req r;
+    r.key_id = key_id;
+    r.dir = dir;
+    r.in = in;
+    r.out = out;
+    r.nbytes = nbytes;
+    r.arrival = arrival;
+    s->reqs.push_back(r);
+    s->pending.push_back(t);
+    if (s->n_submitted == 0 || arrival < s->first_arrival) s->first_arrival = arrival;
+    s->n_submitted++;
+    *ticket = t;
+    return AES_OK;
+}
+
+int aes_srv_submit(aes_server *h, int key_id, int dir, const uint8_t *in_dev, uint8_t *out_dev, size_t nbytes,
+                   uint64_t *ticket) {
+    Server *s = as_server(h);
+    if (!s || !ticket) return AES_E_ARG;
+    int st;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        st = submit_locked(s, key_id, dir, in_dev, out_dev, nbytes, now_s(), ticket);
+    }
+    if (st == AES_OK) s->cv_work.notify_one();
+    return st;
+}
+
+int aes_srv_submit_many(aes_server *h, int n, const int32_t *key_ids, const int32_t *dirs,
+                        const uint64_t *in_devs, const uint64_t *out_devs, const uint64_t *nbytes,
+                        const double *arrival_offsets_s, uint64_t *tickets) {
+    Server *s = as_server(h);
+    if (!s || n < 0 || (n > 0 && (!key_ids || !dirs || !in_devs || !out_devs || !nbytes || !tickets)))
+        return AES_E_ARG;
+    const double t0 = now_s();
+    int first_err = AES_OK;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (int i = 0; i < n; ++i) {
+            const double arr = t0 + (arrival_offsets_s ? arrival_offsets_s[i] : 0.0);
+            const int st = submit_locked(s, key_ids[i], dirs[i], reinterpret_cast<const uint8_t *>(in_devs[i]),
+                                         reinterpret_cast<uint8_t *>(out_devs[i]), nbytes[i], arr, &tickets[i]);
+            if (st != AES_OK) {
+                tickets[i] = 0;
+                if (first_err == AES_OK) first_err = st;
+            }
+        }
+    }
+    s->cv_work.notify_one();
+    return first_err;
+}
+
+int aes_srv_poll(aes_server *h, uint64_t ticket, int *done, int *status, double *latency_s) {
+    Server *s = as_server(h);
+    if (!s || !done) return AES_E_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    const Req *r = s->find(ticket);
+    if (!r || r->released) return AES_E_NOTFOUND;
+    *done = r->done ? 1 : 0;
+    if (status) *status = r->done ? r->status : AES_OK;
+    if (latency_s) *latency_s = r->done ? r->done_t - r->arrival : -1.0;
+    return AES_OK;
+}
+
+int aes_srv_wait(aes_server *h, uint64_t ticket, int timeout_ms, int *status, double *latency_s) {
+    Server *s = as_server(h);
+    if (!s || timeout_ms < 0) return AES_E_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    if (!s->find(ticket) || s->find(ticket)->released) return AES_E_NOTFOUND;
+    const bool ok = s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] {
+        const Req *r = s->find(ticket);
+        return !r || r->done;
+    });
+    const Req *r = s->find(ticket);
+    if (!r) return AES_E_NOTFOUND;
+    if (!ok) return AES_E_TIMEOUT;
+    if (status) *status = r->status;
+    if (latency_s) *latency_s = r->done_t - r->arrival;
+    return AES_OK;
+}
+
+int aes_srv_drain(aes_server *h, int timeout_ms) {
+    Server *s = as_server(h);
+    if (!s || timeout_ms < 0) return AES_E_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    const bool ok = s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms),
+                                        [&] { return s->n_completed >= s->n_submitted; });
+    return ok ? AES_OK : AES_E_TIMEOUT;
+}
+
+int aes_srv_results(aes_server *h, int n, const uint64_t *tickets, int32_t *status, double *latency_s,
+                    double *queue_s, int release) {
+    Server *s = as_server(h);
+    if (!s || n < 0 || (n > 0 && !tickets)) return AES_E_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    int missing = 0;
+    for (int i = 0; i < n; ++i) {
+        Req *r = s->find(tickets[i]);
+        if (!r || r->released || !r->done) {
+            ++missing;
+            if (status) status[i] = (!r || r->released) ? AES_E_NOTFOUND : AES_E_BUSY;
+            if (latency_s) latency_s[i] = -1.0;
+            if (queue_s) queue_s[i] = -1.0;
+            continue;
+        }
+        if (status) status[i] = r->status;
+        if (latency_s) latency_s[i] = r->done_t - r->arrival;
+        if (queue_s) queue_s[i] = r->admitted - r->arrival;
+        if (release) r->released = true;
+    }
+    while (!s->reqs.empty() && s->reqs.front().released) {
+        s->reqs.pop_front();
+        s->base++;
+    }
+    return missing == 0 ? AES_OK : AES_E_BUSY;
+}
+
+int aes_srv_stats(aes_server *h, aes_srv_stats_t *out) {
+    Server *s = as_server(h);
+    if (!s || !out) return AES_E_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    out->submitted = s->n_submitted;
+    out->completed = s->n_completed;
+    out->batches = s->n_batches;
+    out->bytes_completed = s->bytes_completed;
+    out->inflight_bytes = s->inflight;
+    out->peak_inflight_bytes = s->peak_inflight;
+    out->pending = s->pending.size();
+    out->busy_s = s->last_done > s->first_arrival ? s->last_done - s->first_arrival : 0.0;
+    out->worker_status = s->worker_error;
+    return AES_OK;
+}
+
+int aes_srv_destroy(aes_server *h) {
+    Server *s = as_server(h);
+    if (!s) return AES_OK;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    cudaSetDevice(s->dev);
+    free_server(s);
+    return AES_OK;
+}
+
+}  // extern "C"

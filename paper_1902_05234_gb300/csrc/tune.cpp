@@ -1,21 +1,153 @@
-// tune.cpp -- launch configuration choice for the single-buffer kernels.
+// tune.cpp -- launch-configuration choice: size-adaptive defaults and an
+// autotuner that times candidate configurations on the caller's buffers.
+//
+// The single-buffer kernels are tuned per (SM count, direction, Nr, size
+// class), size class = floor(log4(nblocks)); the batch kernel per SM count.
+// Tuned entries live in memory and, when AESGB_TUNE_CACHE names a file, are
+// loaded from it on first use and written back after every tuning run.  The
+// file is plain text, one entry per line:
+//   ecb   <sms> <dir> <nr> <class> <threads> <blocks_per_thread> <layout> <ctas_per_sm>
+//   batch <sms> <threads> <blocks_per_thread> <chunk_passes> <ctas_per_sm>
+#include <cuda_runtime.h>
+
 #include <cstddef>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "batch_internal.h"
 #include "capi_internal.h"
 
 namespace aesgb {
+namespace {
 
-aes_launch_cfg default_cfg(int /*dir*/, int /*nrounds*/, size_t /*nblocks*/) {
+using EcbKey = std::tuple<int, int, int, int>;  // sms, dir, nr, class
+std::mutex g_mu;
+std::map<EcbKey, aes_launch_cfg> g_ecb;
+std::map<int, aes_batch_cfg> g_batch;  // sms -> cfg
+bool g_env_loaded = false;
+
+int size_class(size_t nblocks) {
+    int c = 0;
+    while (nblocks >= 4 && c < 24) {
+        nblocks >>= 2;
+        ++c;
+    }
+    return c;
+}
+
+int current_sms() {
+    int dev = 0;
+    if (current_device(&dev) != AES_OK) return 0;
+    const int s = sm_count(dev);
+    return s > 0 ? s : 0;
+}
+
+int load_file_locked(const char *path) {
+    FILE *f = std::fopen(path, "r");
+    if (!f) return AES_E_ARG;
+    char line[256];
+    while (std::fgets(line, sizeof line, f)) {
+        int a[8];
+        if (std::sscanf(line, "ecb %d %d %d %d %d %d %d %d", &a[0], &a[1], &a[2], &a[3], &a[4], &a[5], &a[6],
+                        &a[7]) == 8) {
+            aes_launch_cfg c{a[4], a[5], a[6], a[7]};
+            if (validate_cfg(c) == AES_OK) g_ecb[EcbKey{a[0], a[1], a[2], a[3]}] = c;
+        } else if (std::sscanf(line, "batch %d %d %d %d %d", &a[0], &a[1], &a[2], &a[3], &a[4]) == 5) {
+            aes_batch_cfg c{a[1], a[2], a[3], a[4]};
+            if (validate_batch_cfg(c) == AES_OK) g_batch[a[0]] = c;
+        }
+    }
+    std::fclose(f);
+    return AES_OK;
+}
+
+int save_file_locked(const char *path) {
+    FILE *f = std::fopen(path, "w");
+    if (!f) return AES_E_ARG;
+    std::fprintf(f, "# aesgb tune cache v1\n");
+    for (const auto &kv : g_ecb) {
+        const auto &k = kv.first;
+        const auto &c = kv.second;
+        std::fprintf(f, "ecb %d %d %d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k),
+                     std::get<3>(k), c.threads, c.blocks_per_thread, c.layout, c.ctas_per_sm);
+    }
+    for (const auto &kv : g_batch)
+        std::fprintf(f, "batch %d %d %d %d %d\n", kv.first, kv.second.threads, kv.second.blocks_per_thread,
+                     kv.second.chunk_passes, kv.second.ctas_per_sm);
+    const bool ok = std::fclose(f) == 0;
+    return ok ? AES_OK : AES_E_ARG;
+}
+
+void load_env_locked() {
+    if (g_env_loaded) return;
+    g_env_loaded = true;
+    const char *p = std::getenv("AESGB_TUNE_CACHE");
+    if (p && *p) (void)load_file_locked(p);
+}
+
+void save_env_locked() {
+    const char *p = std::getenv("AESGB_TUNE_CACHE");
+    if (p && *p) (void)save_file_locked(p);
+}
+
+// Time `launch` (already validated) over `reps` launches after one warm-up.
+template <class F>
+float time_launches(F launch, cudaStream_t s, int reps, int *status) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        *status = AES_E_CUDA;
+        return 0.f;
+    }
+    int st = launch();
+    if (st == AES_OK) st = cudaEventRecord(a, s) == cudaSuccess ? AES_OK : AES_E_CUDA;
+    for (int r = 0; r < reps && st == AES_OK; ++r) st = launch();
+    if (st == AES_OK) st = cudaEventRecord(b, s) == cudaSuccess ? AES_OK : AES_E_CUDA;
+    float ms = 0.f;
+    if (st == AES_OK) st = cudaEventSynchronize(b) == cudaSuccess ? AES_OK : AES_E_CUDA;
+    if (st == AES_OK) st = cudaEventElapsedTime(&ms, a, b) == cudaSuccess ? AES_OK : AES_E_CUDA;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    *status = st;
+    return ms / static_cast<float>(reps);
+}
+
+}  // namespace
+
+// Untuned choice: 2 blocks per thread and 1,024 threads when the buffer fills
+// every SM at least once over; smaller buffers get 1 block per thread and as
+// few threads per CTA as spread the work over all SMs.
+aes_launch_cfg default_cfg(int /*dir*/, int /*nrounds*/, size_t nblocks) {
     aes_launch_cfg c;
-    c.threads = 1024;
-    c.blocks_per_thread = 2;
     c.layout = AES_LAYOUT_R4;
     c.ctas_per_sm = 1;
+    const size_t sms = static_cast<size_t>(current_sms() > 0 ? current_sms() : 152);
+    if (nblocks >= sms * 2048) {
+        c.threads = 1024;
+        c.blocks_per_thread = 2;
+        return c;
+    }
+    size_t per_sm = (nblocks + sms - 1) / sms;
+    per_sm = (per_sm + 31) / 32 * 32;
+    c.threads = static_cast<int32_t>(per_sm < 128 ? 128 : (per_sm > 1024 ? 1024 : per_sm));
+    c.blocks_per_thread = 1;
     return c;
 }
 
 aes_launch_cfg tuned_or_default_cfg(int dir, int nrounds, size_t nblocks) {
+    const int sms = current_sms();
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        load_env_locked();
+        if (!g_ecb.empty()) {
+            auto it = g_ecb.find(EcbKey{sms, dir, nrounds, size_class(nblocks)});
+            if (it != g_ecb.end()) return it->second;
+        }
+    }
     return default_cfg(dir, nrounds, nblocks);
 }
 
@@ -28,6 +160,128 @@ aes_batch_cfg default_batch_cfg() {
     return c;
 }
 
-aes_batch_cfg batch_cfg_for(int /*n*/) { return default_batch_cfg(); }
+aes_batch_cfg batch_cfg_for(int /*n*/) {
+    const int sms = current_sms();
+    std::lock_guard<std::mutex> lk(g_mu);
+    load_env_locked();
+    auto it = g_batch.find(sms);
+    return it != g_batch.end() ? it->second : default_batch_cfg();
+}
 
 }  // namespace aesgb
+
+using namespace aesgb;
+
+extern "C" {
+
+int aes_tune_ecb(int dir, int nrounds, const uint32_t *rk, const uint8_t *in, uint8_t *out, size_t nblocks,
+                 void *stream, aes_launch_cfg *best) {
+    if (dir != 0 && dir != 1) return AES_E_ARG;
+    int st = check_nrounds(nrounds);
+    if (st != AES_OK) return st;
+    if (!rk || nblocks == 0) return AES_E_ARG;
+    st = check_buffers(in, out, nblocks);
+    if (st != AES_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<aes_launch_cfg> cands;
+    for (int layout : {AES_LAYOUT_R4, AES_LAYOUT_R1})
+        for (int nb : {1, 2, 4})
+            for (int th : {128, 256, 512, 768, 1024}) {
+                if (th > (nb >= 4 ? 512 : 1024)) continue;
+                cands.push_back(aes_launch_cfg{th, nb, layout, 0});
+            }
+    cands.push_back(default_cfg(dir, nrounds, nblocks));
+    const int reps = nblocks >= (size_t(1) << 24) ? 2 : 5;
+    float best_ms = 1e30f;
+    aes_launch_cfg best_cfg = cands.back();
+    for (const auto &c : cands) {
+        int tst = AES_OK;
+        const float ms = time_launches([&] { return launch_ecb(dir, rk, nrounds, in, out, nblocks, c, s); }, s,
+                                       reps, &tst);
+        if (tst != AES_OK) continue;  // e.g. a configuration that does not fit
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_cfg = c;
+        }
+    }
+    if (best_ms >= 1e29f) return AES_E_CUDA;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        load_env_locked();
+        g_ecb[EcbKey{current_sms(), dir, nrounds, size_class(nblocks)}] = best_cfg;
+        save_env_locked();
+    }
+    if (best) *best = best_cfg;
+    return AES_OK;
+}
+
+int aes_tune_batch(const aes_desc *desc_dev, int n, void *ws, size_t ws_bytes, void *stream, aes_batch_cfg *best) {
+    if (!desc_dev || n <= 0 || !ws) return AES_E_ARG;
+    if (ws_bytes < batch_ws_bytes(n)) return AES_E_RANGE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    float best_ms = 1e30f;
+    aes_batch_cfg best_cfg = default_batch_cfg();
+    for (int nb : {1, 2})
+        for (int th : {256, 384, 512})
+            for (int passes : {8, 16, 32, 64}) {
+                const aes_batch_cfg c{th, nb, passes, 1};
+                int tst = AES_OK;
+                const float ms = time_launches(
+                    [&] { return aes_ecb_batch_ws(desc_dev, n, ws, ws_bytes, nullptr, &c, stream); }, s, 2, &tst);
+                if (tst != AES_OK) continue;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best_cfg = c;
+                }
+            }
+    if (best_ms >= 1e29f) return AES_E_CUDA;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        load_env_locked();
+        g_batch[current_sms()] = best_cfg;
+        save_env_locked();
+    }
+    if (best) *best = best_cfg;
+    return AES_OK;
+}
+
+int aes_tune_save(const char *path) {
+    if (!path) return AES_E_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    return save_file_locked(path);
+}
+
+int aes_tune_load(const char *path) {
+    if (!path) return AES_E_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_env_loaded = true;
+    return load_file_locked(path);
+}
+
+int aes_tune_clear(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_ecb.clear();
+    g_batch.clear();
+    g_env_loaded = true;  // do not reload the environment file behind the caller's back
+    return AES_OK;
+}
+
+int aes_tune_set_ecb(int dir, int nrounds, size_t nblocks, const aes_launch_cfg *cfg) {
+    if ((dir != 0 && dir != 1) || !cfg) return AES_E_ARG;
+    int st = check_nrounds(nrounds);
+    if (st != AES_OK) return st;
+    st = validate_cfg(*cfg);
+    if (st != AES_OK) return st;
+    std::lock_guard<std::mutex> lk(g_mu);
+    load_env_locked();
+    g_ecb[EcbKey{current_sms(), dir, nrounds, size_class(nblocks)}] = *cfg;
+    return AES_OK;
+}
+
+int aes_batch_get_cfg(int n, aes_batch_cfg *cfg) {
+    if (!cfg) return AES_E_ARG;
+    *cfg = batch_cfg_for(n);
+    return AES_OK;
+}
+
+}  // extern "C"

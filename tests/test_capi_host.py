@@ -91,3 +91,43 @@ def test_default_cfg_is_valid():
         for nr in (10, 12, 14):
             c = aesgb.aes_ecb_get_cfg(d, nr, 1 << 20)
             assert c.threads % 32 == 0 and c.blocks_per_thread in (1, 2, 4)
+
+
+def test_tune_cache_file_roundtrip(tmp_path):
+    """Tuned entries set by hand survive save / clear / load (host logic)."""
+    aesgb.aes_tune_clear()
+    try:
+        c = aesgb.make_cfg(threads=256, blocks_per_thread=4, layout=aesgb.LAYOUT_R1, ctas_per_sm=0)
+        aesgb.aes_tune_set_ecb(1, 12, 1 << 22, c)
+        got = aesgb.aes_ecb_get_cfg(1, 12, 1 << 22)
+        assert got.as_dict() == c.as_dict()
+        other = aesgb.aes_ecb_get_cfg(0, 12, 1 << 22)          # other direction: default
+        assert other.layout == aesgb.LAYOUT_R4
+        path = str(tmp_path / "tune.txt")
+        aesgb.aes_tune_save(path)
+        text = open(path).read()
+        assert "ecb" in text and " 256 4 1 0" in text
+        aesgb.aes_tune_clear()
+        assert aesgb.aes_ecb_get_cfg(1, 12, 1 << 22).layout == aesgb.LAYOUT_R4
+        aesgb.aes_tune_load(path)
+        assert aesgb.aes_ecb_get_cfg(1, 12, 1 << 22).as_dict() == c.as_dict()
+        # a different size class is not affected
+        assert aesgb.aes_ecb_get_cfg(1, 12, 1 << 10).layout == aesgb.LAYOUT_R4
+        with pytest.raises(aesgb.AesError):
+            aesgb.aes_tune_set_ecb(0, 10, 100, aesgb.make_cfg(threads=2048))
+    finally:
+        aesgb.aes_tune_clear()
+
+
+def test_batch_default_cfg_valid():
+    c = aesgb.aes_batch_get_cfg(4096)
+    assert c.threads <= 512 and c.blocks_per_thread in (1, 2, 4) and c.chunk_passes >= 1
+
+
+def test_server_create_fails_cleanly_without_gpu():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(aesgb.AesError):
+        aesgb.aes_srv_create(1 << 20, 4, 8, 1)
+    aesgb.aes_srv_destroy(0)          # a null handle is a no-op

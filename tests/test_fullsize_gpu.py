@@ -1,0 +1,151 @@
+"""Parity at the full workload sizes, in the launch configuration the benchmark
+times (the library's default for the size): sampled windows checked against
+the oracle, properties checked over the whole buffer on the device.
+
+* single buffers of 4 GiB, AES-128/192/256: 10 windows of 256 KiB (first, last,
+  eight seeded random) against the oracle; decrypt(encrypt(x)) == x over all
+  4 GiB on the device.
+* the 4,096-message batch (5.2 GB): every message equal to the single-buffer
+  path; all messages up to 16 KiB and a 4 KiB window of every 8th larger one
+  against the oracle.
+* the stress case: AES-256 decryption in place over 16 GiB of 64 MiB regions
+  cycling uniform random / all-zero / one block repeated; 32 windows of 1 MiB
+  (region boundaries included) against the oracle, and every all-zero or
+  periodic region decrypted to one repeated block equal to the oracle's
+  decryption of that block (ECB's identical-block invariant).
+"""
+import numpy as np
+import pytest
+
+from paper_1902_05234_gb300 import aesgb
+from paper_1902_05234_gb300 import workloads as wl
+from gpu_util import torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+GIB = 1 << 30
+MIB = 1 << 20
+
+
+def _fill_random(torch, t, seed):
+    g = torch.Generator(device="cuda")
+    g.manual_seed(wl.BASE_SEED + seed)
+    t.random_(0, 256, generator=g)
+
+
+@pytest.mark.parametrize("keybits", [128, 192, 256])
+def test_4gib_single_buffer_windows_and_roundtrip(orc, keybits):
+    torch = torch_cuda()
+    nbytes = 4 * GIB
+    n = nbytes // 16
+    x = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    _fill_random(torch, x, 50 + keybits)
+    y = torch.empty_like(x)
+    key = wl.random_key(keybits, 50).tobytes()
+    enc, dec, nr = aesgb.aes_expand_key(keybits, key)
+    aesgb.aes_ecb_encrypt(enc, nr, x, y, n)
+    torch.cuda.synchronize()
+    win = 256 * 1024
+    g = wl.rng(51)
+    starts = [0, nbytes - win] + [int(v) // 16 * 16 for v in g.integers(0, nbytes - win, 8)]
+    for s in starts:
+        got = y[s:s + win].cpu().numpy()
+        exp = orc.ecb(0, key, x[s:s + win].cpu().numpy(), nthreads=16)
+        assert np.array_equal(got, exp), f"window at {s}"
+    aesgb.aes_ecb_decrypt(dec, nr, y, y, n)       # in place
+    torch.cuda.synchronize()
+    assert torch.equal(x, y)
+
+
+def test_batch_4096_messages_fullsize(orc):
+    torch = torch_cuda()
+    n = 4096
+    lengths, keybits, dirs = wl.batch_workload(n)
+    offs = np.zeros(n + 1, np.int64)
+    np.cumsum(lengths, out=offs[1:])
+    total = int(offs[-1])
+    src = torch.empty(total, dtype=torch.uint8, device="cuda")
+    _fill_random(torch, src, 52)
+    dst = torch.full_like(src, 0x5A)
+    ref = torch.empty_like(src)
+    g = wl.rng(52)
+    keys = [g.integers(0, 256, int(kb) // 8, dtype=np.uint8).tobytes() for kb in keybits]
+    rks = np.zeros((n, 64), np.uint32)
+    nrs = np.zeros(n, np.int64)
+    for i in range(n):
+        enc, dec, nr = aesgb.aes_expand_key(int(keybits[i]), keys[i])
+        rks[i, :60] = enc if dirs[i] == 0 else dec
+        nrs[i] = nr
+        a, b = src.data_ptr() + int(offs[i]), ref.data_ptr() + int(offs[i])
+        (aesgb.aes_ecb_encrypt if dirs[i] == 0 else aesgb.aes_ecb_decrypt)(rks[i, :60], nr, a, b,
+                                                                         int(lengths[i]) // 16)
+    rk_dev = torch.from_numpy(rks.view(np.uint8).reshape(-1)).cuda()
+    table = aesgb.pack_descs(rk_dev.data_ptr() + 256 * np.arange(n, dtype=np.uint64),
+                             src.data_ptr() + offs[:-1].astype(np.uint64),
+                             dst.data_ptr() + offs[:-1].astype(np.uint64), lengths // 16, nrs, dirs)
+    desc = torch.from_numpy(table.view(np.uint8).copy()).cuda()
+    ws_bytes = aesgb.aes_batch_workspace_bytes(n)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+    status = torch.full((n,), 9, dtype=torch.int32, device="cuda")
+    aesgb.aes_ecb_batch_ws(desc, n, ws, ws_bytes, status)
+    torch.cuda.synchronize()
+    assert bool((status == 0).all())
+    assert torch.equal(dst, ref)
+    host_src = None
+    for i in range(n):
+        ln = int(lengths[i])
+        o = int(offs[i])
+        if ln <= 16 * 1024:
+            m = src[o:o + ln].cpu().numpy()
+            exp = orc.ecb(int(dirs[i]), keys[i], m, nthreads=1)
+            assert np.array_equal(dst[o:o + ln].cpu().numpy(), exp), i
+        elif i % 8 == 0:
+            w = 4096
+            s = o + (ln - w) // 2 // 16 * 16
+            m = src[s:s + w].cpu().numpy()
+            exp = orc.ecb(int(dirs[i]), keys[i], m, nthreads=1)
+            assert np.array_equal(dst[s:s + w].cpu().numpy(), exp), i
+    del host_src
+
+
+def test_stress_16gib_aes256_decrypt_in_place(orc):
+    torch = torch_cuda()
+    total = 16 * GIB
+    region = 64 * MIB
+    kinds = wl.stress_region_kinds(total, region)
+    buf = torch.empty(total, dtype=torch.uint8, device="cuda")
+    g = torch.Generator(device="cuda")
+    g.manual_seed(wl.BASE_SEED + 53)
+    hg = wl.rng(53)
+    period_blocks = {}
+    for r, kind in enumerate(kinds.tolist()):
+        sl = buf[r * region:(r + 1) * region]
+        if kind == 0:
+            sl.random_(0, 256, generator=g)
+        elif kind == 1:
+            sl.zero_()
+        else:
+            blk = hg.integers(0, 256, 16, dtype=np.uint8)
+            period_blocks[r] = blk
+            sl.view(-1, 16).copy_(torch.from_numpy(blk).cuda().expand(region // 16, 16))
+    key = wl.random_key(256, 53).tobytes()
+    enc, dec, nr = aesgb.aes_expand_key(256, key)
+    # 32 windows of 1 MiB saved before: region boundaries and seeded random spots
+    w = MIB
+    starts = [region - w // 2, 2 * region - w // 2, 3 * region - w // 2, 0, total - w]
+    starts += [int(v) // 16 * 16 for v in hg.integers(0, total - w, 32 - len(starts))]
+    saved = [(s, buf[s:s + w].cpu().numpy()) for s in starts]
+    aesgb.aes_ecb_decrypt(dec, nr, buf, buf, total // 16)
+    torch.cuda.synchronize()
+    for s, before in saved:
+        exp = orc.ecb(1, key, before, nthreads=16)
+        assert np.array_equal(buf[s:s + w].cpu().numpy(), exp), f"window at {s}"
+    zero_pt = orc.ecb(1, key, np.zeros(16, np.uint8))
+    for r, kind in enumerate(kinds.tolist()):
+        if kind == 0:
+            continue
+        blocks = buf[r * region:(r + 1) * region].view(-1, 16)
+        first = blocks[0].cpu().numpy()
+        exp = zero_pt if kind == 1 else orc.ecb(1, key, period_blocks[r])
+        assert np.array_equal(first, exp), f"region {r}"
+        assert bool((blocks == blocks[0]).all()), f"region {r} not a single repeated block"

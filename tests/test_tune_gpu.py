@@ -1,0 +1,58 @@
+"""The autotuner picks a configuration by timing, the plain entry points use
+it afterwards, and results stay bit-exact."""
+import numpy as np
+import pytest
+
+from paper_1902_05234_gb300 import aesgb
+from paper_1902_05234_gb300 import workloads as wl
+from batch_util import DeviceBatch
+from gpu_util import torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def test_tune_ecb_then_use(orc, tmp_path):
+    torch = torch_cuda()
+    aesgb.aes_tune_clear()
+    try:
+        n = 1 << 20                                  # 16 MiB
+        x = torch.from_numpy(wl.random_bytes(16 * n, 80)).cuda()
+        y = torch.empty_like(x)
+        key = wl.random_key(192, 80).tobytes()
+        enc, dec, nr = aesgb.aes_expand_key(192, key)
+        best = aesgb.aes_tune_ecb(1, nr, dec, x, y, n)
+        assert best.layout in (0, 1) and best.blocks_per_thread in (1, 2, 4)
+        assert aesgb.aes_ecb_get_cfg(1, nr, n).as_dict() == best.as_dict()
+        aesgb.aes_ecb_decrypt(dec, nr, x, y, n)
+        torch.cuda.synchronize()
+        w = 65536
+        assert np.array_equal(y[:w].cpu().numpy(), orc.ecb(1, key, x[:w].cpu().numpy(), nthreads=8))
+        assert np.array_equal(y[-w:].cpu().numpy(), orc.ecb(1, key, x[-w:].cpu().numpy(), nthreads=8))
+        path = str(tmp_path / "t.txt")
+        aesgb.aes_tune_save(path)
+        assert "ecb" in open(path).read()
+    finally:
+        aesgb.aes_tune_clear()
+
+
+def test_tune_batch_then_use(orc):
+    torch = torch_cuda()
+    aesgb.aes_tune_clear()
+    try:
+        g = wl.rng(81)
+        lengths = wl.log_uniform_lengths(200, 16, 1 << 20, g)
+        b = DeviceBatch(torch, lengths, g.choice(np.array([128, 192, 256]), size=200),
+                        g.integers(0, 2, size=200), seed=81)
+        ws, nbytes = b.workspace()
+        best = aesgb.aes_tune_batch(b.desc_dev, b.n, ws, nbytes)
+        got = aesgb.aes_batch_get_cfg(b.n)
+        assert (got.threads, got.blocks_per_thread, got.chunk_passes) == \
+               (best.threads, best.blocks_per_thread, best.chunk_passes)
+        b.out_dev.fill_(0x5A)
+        aesgb.aes_ecb_batch_ws(b.desc_dev, b.n, ws, nbytes)
+        out = b.output()
+        for i in range(0, b.n, 7):
+            exp = orc.ecb(int(b.dirs[i]), b.keys[i], b.message(b.data, i), nthreads=4)
+            assert np.array_equal(b.message(out, i), exp)
+    finally:
+        aesgb.aes_tune_clear()
