@@ -13,8 +13,9 @@ Additional objects on the same line:
   roofline     the encryption kernel against its bound, the shared-memory lookup
                rate (16 lookups of 4 B per block per round; 32 lanes x 4 B per clock
                per SM), at the SM clock sampled during the timed region.
-  e2e          the same two passes through aes_ecb_host: page-locked host buffers,
-               host->device and device->host copies inside the timed region.
+  e2e          the same two passes through aes_ecb_host_direct on page-locked host
+               buffers: the kernel itself reads the input from and writes the output to
+               host memory, so every byte crosses the host link inside the timed region.
   cpu_baseline the CPU oracle timed on this host's cores on a bounded sample.
   sweep        single-buffer Gbit/s over 1 MiB..4 GiB x AES-128/192/256 x enc/dec.
   clocks       nvidia-smi SM clock and throttle reasons sampled while timing.
@@ -61,6 +62,10 @@ def parse_args():
     p.add_argument("--no-served", action="store_true")
     p.add_argument("--no-tune", action="store_true")
     p.add_argument("--served-requests", type=int, default=20000)
+    p.add_argument("--study", action="store_true",
+                   help="placement / granularity study (the paper's section 4 design axis) instead of the bench")
+    p.add_argument("--study-reps", type=int, default=5)
+    p.add_argument("--study-warmup", type=int, default=2)
     return p.parse_args()
 
 
@@ -499,6 +504,58 @@ def run_served(torch, aesgb, dev, n_req=20000, loads=(0.1, 0.2, 0.3, 0.4, 0.5, 0
     return out
 
 
+STUDY_VARIANTS = [  # (label, layout, blocks/thread, threads)
+    ("constant memory (paper 4.2), 16 B/thread", 3, 1, 256),
+    ("shared, 4 plain tables, 16 B/thread", 2, 1, 1024),
+    ("shared, 1 replicated table + rotations, 16 B/thread", 1, 1, 1024),
+    ("shared, 1 replicated table + rotations, 32 B/thread", 1, 2, 1024),
+    ("shared, 4 replicated tables, 16 B/thread", 0, 1, 1024),
+    ("shared, 4 replicated tables, 32 B/thread", 0, 2, 1024),
+    ("shared, 4 replicated tables, 64 B/thread", 0, 4, 512),
+]
+
+
+def run_study(args):
+    """Every table placement and granularity on one AES-128 encryption of
+    --bytes, each launched --study-warmup + --study-reps times (1 + 0 under ncu
+    gives one launch per variant, in the order listed)."""
+    import torch
+    from paper_1902_05234_gb300 import aesgb
+    from paper_1902_05234_gb300 import workloads as wl
+    torch.cuda.set_device(0)
+    nbytes = args.bytes // 16 * 16
+    n = nbytes // 16
+    x = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    g = torch.Generator(device="cuda")
+    g.manual_seed(wl.BASE_SEED + 100)
+    x.random_(0, 256, generator=g)
+    y = torch.empty_like(x)
+    ref = torch.empty_like(x)
+    enc, _, nr = aesgb.aes_expand_key(128, wl.random_key(128, 100).tobytes())
+    rows = []
+    for i, (label, layout, nb, threads) in enumerate(STUDY_VARIANTS):
+        cfg = aesgb.make_cfg(threads, nb, layout, 0)
+        for _ in range(args.study_warmup):
+            aesgb.aes_ecb_crypt_cfg(0, enc, nr, x, y, n, cfg)
+        ms = None
+        if args.study_reps > 0:
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            for _ in range(args.study_reps):
+                aesgb.aes_ecb_crypt_cfg(0, enc, nr, x, y, n, cfg)
+            e.record()
+            e.synchronize()
+            ms = s.elapsed_time(e) / args.study_reps
+        torch.cuda.synchronize()
+        if i == 0:
+            ref.copy_(y)
+        rows.append({"variant": label, "cfg": repr(cfg), "ms": None if ms is None else round(ms, 4),
+                     "gbps": None if ms is None else round(nbytes * 8 / ms / 1e6, 1),
+                     "same_output": bool(torch.equal(y, ref))})
+    print(json.dumps({"study": "AES-128 ECB encryption, table placement x granularity",
+                      "bytes": nbytes, "rows": rows}), flush=True)
+
+
 def run_gb300(args, dist: Dist):
     import torch
     from paper_1902_05234_gb300 import aesgb
@@ -635,13 +692,11 @@ def run_e2e(torch, aesgb, key, keybits, pt_dev, nbytes, stream, dist, K):
     h_ct = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
     h_back = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
     h_pt.copy_(pt_dev)
-    stage_bytes = 3 * 64 * MIB
-    stage = torch.empty(stage_bytes, dtype=torch.uint8, device=pt_dev.device)
 
     def e2e_step():
         enc, dec, nr = aesgb.aes_expand_key(keybits, key)
-        aesgb.aes_ecb_host(0, enc, nr, h_pt, h_ct, nblocks, stage, stage_bytes, stream)
-        aesgb.aes_ecb_host(1, dec, nr, h_ct, h_back, nblocks, stage, stage_bytes, stream)
+        aesgb.aes_ecb_host_direct(0, enc, nr, h_pt, h_ct, nblocks, stream)
+        aesgb.aes_ecb_host_direct(1, dec, nr, h_ct, h_back, nblocks, stream)
 
     for _ in range(2):
         e2e_step()
@@ -661,7 +716,8 @@ def run_e2e(torch, aesgb, key, keybits, pt_dev, nbytes, stream, dist, K):
         raise SystemExit("bench e2e: decrypt(encrypt(x)) != x")
     return {"value": round(2 * nbytes * 8 * dist.world / ms / 1e6, 2), "unit": UNIT,
             "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": 2 * nbytes,
-            "ms_per_step": round(ms, 4), "api": "aes_ecb_host (3 x 64 MiB staging slots)",
+            "ms_per_step": round(ms, 4),
+            "api": "aes_ecb_host_direct (kernel reads/writes page-locked host memory over NVLink-C2C)",
             "steps": iters}
 
 
@@ -671,6 +727,8 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, dist)
+        elif args.study:
+            run_study(args)
         else:
             run_gb300(args, dist)
     finally:

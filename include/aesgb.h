@@ -241,6 +241,36 @@ int aes_ecb_host(int dir, const uint32_t *rk, int nrounds, const uint8_t *host_i
                  uint8_t *host_out, size_t nblocks, uint8_t *dev_buf, size_t dev_buf_bytes,
                  void *stream);
 
+/* ECB directly on page-locked HOST memory: host_in and host_out must be
+ * page-locked and mapped for the device (cudaHostAlloc / cudaHostRegister with
+ * mapping, or torch's pin_memory), else AES_E_ARG.  The kernel reads and
+ * writes them over the host link itself -- no staging buffer, no copies, no
+ * internal streams; throughput is that of the link.  Same cipher, rk and
+ * overlap rules as aes_ecb_encrypt/decrypt; asynchronous on `stream`.  The
+ * buffers must hold nblocks*16 bytes (only their first bytes are checked). */
+int aes_ecb_host_direct(int dir, const uint32_t *rk, int nrounds, const uint8_t *host_in, uint8_t *host_out,
+                        size_t nblocks, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Other parallel modes on the same cipher                                   */
+/* ------------------------------------------------------------------------ */
+
+/* CTR (section 3.1.5, eq (5); Table 1: parallel like ECB): C_i = P_i xor
+ * E(T_i) with T_i = ctr0 + i as a 128-bit big-endian integer mod 2^128 (ctr0,
+ * HOST, 16 bytes, is the counter block of the first block).  The same call
+ * decrypts.  rk = rk_enc (HOST); in/out DEVICE as for ECB, in place allowed. */
+int aes_ctr_crypt(const uint32_t *rk, int nrounds, const uint8_t *ctr0, const uint8_t *in, uint8_t *out,
+                  size_t nblocks, void *stream);
+
+/* CBC decryption (section 3.1.2, with eq (2) read as C_i = E(P_i xor C_{i-1})
+ * per NIST SP 800-38A): P_i = D(C_i) xor C_{i-1}, C_{-1} = iv (HOST, 16 bytes).
+ * Every block needs only two ciphertext blocks, so it runs in parallel.
+ * rk_dec from aes_expand_key; in/out DEVICE, disjoint (in place is
+ * AES_E_OVERLAP: ciphertext must outlive the plaintext written next to it).
+ * CBC encryption chains block to block and is not offered (Table 1). */
+int aes_cbc_decrypt(const uint32_t *rk_dec, int nrounds, const uint8_t *iv, const uint8_t *in, uint8_t *out,
+                    size_t nblocks, void *stream);
+
 /* Release every resource the library created lazily (internal streams and
  * events, batch workspaces, tuner state) on all devices.  Call with no work
  * of the library in flight. */

@@ -103,6 +103,9 @@ _SIGNATURES = {
     "aes_batch_graph_launch": (_i, [_vp, _vp]),
     "aes_batch_graph_destroy": (_i, [_vp]),
     "aes_shutdown": (_i, []),
+    "aes_ecb_host_direct": (_i, [_i, _u32p, _i, _vp, _vp, _sz, _vp]),
+    "aes_ctr_crypt": (_i, [_u32p, _i, _u8p, _vp, _vp, _sz, _vp]),
+    "aes_cbc_decrypt": (_i, [_u32p, _i, _u8p, _vp, _vp, _sz, _vp]),
     "aes_tune_ecb": (_i, [_i, _i, _u32p, _vp, _vp, _sz, _vp, ctypes.POINTER(aes_launch_cfg)]),
     "aes_tune_batch": (_i, [_vp, _i, _vp, _sz, _vp, ctypes.POINTER(aes_batch_cfg)]),
     "aes_tune_set_ecb": (_i, [_i, _i, _sz, ctypes.POINTER(aes_launch_cfg)]),
@@ -388,6 +391,34 @@ def aes_srv_stats(srv: int) -> dict:
 
 def aes_srv_destroy(srv: int) -> None:
     _check(lib().aes_srv_destroy(_vp(srv)), "aes_srv_destroy")
+
+
+def aes_ecb_host_direct(direction: int, rk, nrounds: int, host_in, host_out, nblocks: int, stream=None) -> None:
+    p, _keep = _rk_arg(rk)
+    _check(lib().aes_ecb_host_direct(int(direction), p, int(nrounds), _ptr(host_in), _ptr(host_out), int(nblocks),
+                                     _stream(stream)), "aes_ecb_host_direct")
+
+
+def _block16(b):
+    a = np.ascontiguousarray(np.frombuffer(bytes(b), np.uint8) if isinstance(b, (bytes, bytearray))
+                             else np.asarray(b, np.uint8))
+    if a.size != 16:
+        raise AesError(-1, "a counter block / IV is 16 bytes")
+    return a
+
+
+def aes_ctr_crypt(rk, nrounds: int, ctr0, in_, out, nblocks: int, stream=None) -> None:
+    p, _keep = _rk_arg(rk)
+    c = _block16(ctr0)
+    _check(lib().aes_ctr_crypt(p, int(nrounds), c.ctypes.data_as(_u8p), _ptr(in_), _ptr(out), int(nblocks),
+                               _stream(stream)), "aes_ctr_crypt")
+
+
+def aes_cbc_decrypt(rk_dec, nrounds: int, iv, in_, out, nblocks: int, stream=None) -> None:
+    p, _keep = _rk_arg(rk_dec)
+    v = _block16(iv)
+    _check(lib().aes_cbc_decrypt(p, int(nrounds), v.ctypes.data_as(_u8p), _ptr(in_), _ptr(out), int(nblocks),
+                                 _stream(stream)), "aes_cbc_decrypt")
 
 
 def aes_shutdown() -> None:

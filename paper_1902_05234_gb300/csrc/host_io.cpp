@@ -140,3 +140,29 @@ extern "C" int aes_ecb_host(int dir, const uint32_t *rk, int nrounds, const uint
     if (a != b && a < b + len && b < a + len) return AES_E_OVERLAP;
     return host_pipeline(dir, rk, nrounds, host_in, host_out, nblocks, dev_buf, dev_buf_bytes, stream);
 }
+
+extern "C" int aes_ecb_host_direct(int dir, const uint32_t *rk, int nrounds, const uint8_t *host_in,
+                                   uint8_t *host_out, size_t nblocks, void *stream) {
+    if (dir != 0 && dir != 1) return AES_E_ARG;
+    int st = check_nrounds(nrounds);
+    if (st != AES_OK) return st;
+    if (!rk) return AES_E_ARG;
+    if (nblocks == 0) return AES_OK;
+    st = check_buffers(host_in, host_out, nblocks);
+    if (st != AES_OK) return st;
+    // both buffers must be page-locked host memory mapped for the device
+    void *dev_ptr[2] = {nullptr, nullptr};
+    const void *host_ptr[2] = {host_in, host_out};
+    for (int i = 0; i < 2; ++i) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, host_ptr[i]) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return AES_E_ARG;
+        }
+        if (a.type != cudaMemoryTypeHost || a.devicePointer == nullptr) return AES_E_ARG;
+        dev_ptr[i] = a.devicePointer;
+    }
+    const aes_launch_cfg cfg = tuned_or_default_cfg(dir, nrounds, nblocks);
+    return launch_ecb(dir, rk, nrounds, static_cast<const uint8_t *>(dev_ptr[0]), static_cast<uint8_t *>(dev_ptr[1]),
+                      nblocks, cfg, stream);
+}
