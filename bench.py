@@ -62,6 +62,8 @@ def parse_args():
     p.add_argument("--no-served", action="store_true")
     p.add_argument("--no-tune", action="store_true")
     p.add_argument("--served-requests", type=int, default=20000)
+    p.add_argument("--batch-n", type=int, default=4096, help="messages in the batched workload")
+    p.add_argument("--batch-max-bytes", type=int, default=16 * MIB, help="largest message of the batched workload")
     p.add_argument("--study", action="store_true",
                    help="placement / granularity study (the paper's section 4 design axis) instead of the bench")
     p.add_argument("--study-reps", type=int, default=5)
@@ -328,7 +330,7 @@ def run_sweep(torch, aesgb, dev):
     return rows
 
 
-def run_batched(torch, aesgb, dev, n=4096, tune=True):
+def run_batched(torch, aesgb, dev, n=4096, tune=True, hi=16 * MIB):
     """Batched workload: 4,096 messages, log-uniform 16 B .. 16 MiB, key size
     uniform over {128,192,256}, direction 50/50 -- one persistent launch from a
     device descriptor table replayed as a CUDA graph, against the same messages
@@ -337,7 +339,7 @@ def run_batched(torch, aesgb, dev, n=4096, tune=True):
     loop with the key schedule per message."""
     import numpy as np
     from paper_1902_05234_gb300 import workloads as wl
-    lengths, keybits, dirs = wl.batch_workload(n)
+    lengths, keybits, dirs = wl.batch_workload(n, hi=hi)
     offs = np.zeros(n + 1, np.int64)
     np.cumsum(lengths, out=offs[1:])
     total = int(offs[-1])
@@ -421,7 +423,7 @@ def run_batched(torch, aesgb, dev, n=4096, tune=True):
     torch.cuda.synchronize()
     ms_loop_py = (time.perf_counter() - t) * 1e3
     gb = total * 8 / 1e9
-    out = {"workload": f"{n} messages, log-uniform 16 B..16 MiB (total {total:,} B), keys uniform over "
+    out = {"workload": f"{n} messages, log-uniform 16 B..{hi // MIB} MiB (total {total:,} B), keys uniform over "
                        f"128/192/256, direction 50/50",
            "total_bytes": total, "ms": round(ms_batch, 4), "gbps": round(gb / (ms_batch / 1e3), 1),
            "loop_graph_ms": round(ms_loop_graph, 4), "loop_graph_gbps": round(gb / (ms_loop_graph / 1e3), 1),
@@ -460,8 +462,12 @@ def run_served(torch, aesgb, dev, n_req=20000, loads=(0.1, 0.2, 0.3, 0.4, 0.5, 0
             kb = int(kg.choice([128, 192, 256]))
             aesgb.aes_srv_put_key(srv, k, kb, kg.integers(0, 256, kb // 8, dtype=np.uint8).tobytes())
 
+        submit_ms = []
+
         def run(offsets):
+            t_sub = time.perf_counter()
             st, tickets = aesgb.aes_srv_submit_many(srv, key_ids, dirs, ins, outs, sizes, offsets)
+            submit_ms.append((time.perf_counter() - t_sub) * 1e3)
             if st != 0:
                 raise SystemExit(f"served: submission refused ({st})")
             aesgb.aes_srv_drain(srv, 600000)
@@ -497,6 +503,7 @@ def run_served(torch, aesgb, dev, n_req=20000, loads=(0.1, 0.2, 0.3, 0.4, 0.5, 0
                        f"(total {total:,} B), 1,024 resident keys (128/192/256), direction 50/50, "
                        f"4 GiB budget, 4 in-flight batches",
            "peak_gbps": round(peak_bps * 8 / 1e9, 1), "sweep": rows,
+           "submit_many_ms": round(statistics.median(submit_ms), 3),
            "identical_across_loads": identical, "batches_total": stats["batches"],
            "peak_inflight_bytes": stats["peak_inflight_bytes"]}
     del src, dst, ref
@@ -640,6 +647,11 @@ def run_gb300(args, dist: Dist):
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    # measured peak of the same bound: the lookup-rate calibration kernel
+    sink = torch.empty(sms * 4096, dtype=torch.uint8, device=dev)
+    cal_lookups, cal_s = aesgb.aes_calibrate_lookup_rate(sink, sink.numel(), stream)
+    del sink
+    measured_lookup_gbs = cal_lookups * 4 / cal_s / 1e9
     roofline = {
         "bound": "smem", "kernel": f"ecb_kernel<encrypt,Nr={nr}>",
         "achieved": round(achieved_gbs, 1), "peak": round(peak_gbs, 1), "unit": "GB/s",
@@ -649,6 +661,10 @@ def run_gb300(args, dist: Dist):
         "peak_basis": f"{sms} SMs x {f_mhz:.0f} MHz (median sampled under load) x 128 B/clk shared-memory "
                       f"lookups (derived from unit counts and the measured clock)",
         "achieved_gbps": round(enc_gbps, 1), "peak_gbps": round(peak_gbps_metric, 1),
+        "measured_peak": {"gbs": round(measured_lookup_gbs, 1),
+                          "lookups_per_clk_per_sm": round(cal_lookups / cal_s / (sms * f_mhz * 1e6), 3),
+                          "frac": round(achieved_gbs / measured_lookup_gbs, 4),
+                          "source": "aes_calibrate_lookup_rate (conflict-free LDS stream, same table layout)"},
         "avg_launch_ms": round(enc_ms, 4),
         "hbm": {"achieved_gbs": round(2 * nbytes / (enc_ms / 1e3) / 1e9, 1), "peak_gbs": hbm_peak,
                 "frac": round(2 * nbytes / (enc_ms / 1e3) / 1e9 / hbm_peak, 4), "peak_source": "measured"},
@@ -675,7 +691,8 @@ def run_gb300(args, dist: Dist):
     if dist.rank == 0 and world == 1 and not args.no_sweep:
         line["sweep"] = run_sweep(torch, aesgb, dev)
     if dist.rank == 0 and world == 1 and not args.no_batched:
-        line["batched"] = run_batched(torch, aesgb, dev, tune=not args.no_tune)
+        line["batched"] = run_batched(torch, aesgb, dev, n=args.batch_n, tune=not args.no_tune,
+                                      hi=args.batch_max_bytes)
     if dist.rank == 0 and world == 1 and not args.no_served:
         line["served"] = run_served(torch, aesgb, dev, n_req=args.served_requests)
     if dist.rank == 0 and world == 1 and not args.no_cpu:

@@ -282,9 +282,10 @@ int aes_shutdown(void);
 /* A request is ECB (eq (1)) of one caller-owned device buffer with a
  * resident key.  The server's dispatcher thread admits requests in arrival
  * order while the bytes in flight (2 x nbytes per admitted, unfinished
- * request: input and output) stay within mem_budget_bytes, packs everything
- * admitted into one batch whenever one of `slots` in-flight batch slots is
- * free, and launches it on that slot's stream (descriptor upload, the plan and
+ * request: input and output) stay within mem_budget_bytes, packs what is
+ * admitted -- at most mem_budget_bytes / slots per batch, so that several
+ * batches queue on the device under load -- into one batch whenever one of
+ * `slots` in-flight batch slots is free, and launches it on that slot's stream (descriptor upload, the plan and
  * persistent batch kernels, status download, completion event).  Requests
  * that arrive while earlier batches run join the next batch; consecutive
  * batches overlap on the device.  Host waits are bounded; nothing waits on the
@@ -388,6 +389,16 @@ int aes_tune_clear(void);
 
 /* Number of SMs of CUDA device `device` (>0), or AES_E_CUDA. */
 int aes_device_sm_count(int device);
+
+/* Measure the sustainable rate of the bound the T-table kernels run into:
+ * independent, bank-conflict-free 4-byte shared-memory lookups (the access
+ * pattern of eq (26) without the rest of the cipher), one CTA of 1,024 threads
+ * per SM.  sink_dev: DEVICE scratch of at least SMs*4096 bytes (only written
+ * in a case that does not occur; it keeps the loads from being removed).
+ * Returns the lookups performed and the seconds they took (synchronises
+ * `stream`); lookups / seconds / (SMs * SM clock) is the measured peak per
+ * SM per clock, against the nominal 32. */
+int aes_calibrate_lookup_rate(void *sink_dev, size_t sink_bytes, void *stream, double *lookups, double *seconds);
 
 /* Copy one of the library's 256-entry tables (built at compile time) from
  * HOST memory, no GPU needed:  which = 0 te0 (eq (22) column packed with row r

@@ -103,6 +103,8 @@ _SIGNATURES = {
     "aes_batch_graph_launch": (_i, [_vp, _vp]),
     "aes_batch_graph_destroy": (_i, [_vp]),
     "aes_shutdown": (_i, []),
+    "aes_calibrate_lookup_rate": (_i, [_vp, _sz, _vp, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]),
     "aes_ecb_host_direct": (_i, [_i, _u32p, _i, _vp, _vp, _sz, _vp]),
     "aes_ctr_crypt": (_i, [_u32p, _i, _u8p, _vp, _vp, _sz, _vp]),
     "aes_cbc_decrypt": (_i, [_u32p, _i, _u8p, _vp, _vp, _sz, _vp]),
@@ -419,6 +421,14 @@ def aes_cbc_decrypt(rk_dec, nrounds: int, iv, in_, out, nblocks: int, stream=Non
     v = _block16(iv)
     _check(lib().aes_cbc_decrypt(p, int(nrounds), v.ctypes.data_as(_u8p), _ptr(in_), _ptr(out), int(nblocks),
                                  _stream(stream)), "aes_cbc_decrypt")
+
+
+def aes_calibrate_lookup_rate(sink_dev, sink_bytes: int, stream=None) -> tuple[float, float]:
+    """(lookups, seconds) of the shared-memory lookup calibration kernel."""
+    n, t = ctypes.c_double(), ctypes.c_double()
+    _check(lib().aes_calibrate_lookup_rate(_ptr(sink_dev), int(sink_bytes), _stream(stream), ctypes.byref(n),
+                                           ctypes.byref(t)), "aes_calibrate_lookup_rate")
+    return float(n.value), float(t.value)
 
 
 def aes_shutdown() -> None:

@@ -6,8 +6,8 @@
 //   * admits requests in arrival order while the bytes in flight (input +
 //     output of every admitted, unfinished request) stay within the budget;
 //     a request that does not fit waits, and so do the ones behind it (FIFO);
-//   * packs every admitted request into one batch as soon as one of the
-//     in-flight slots is free, and launches it (descriptor upload, plan and
+//   * packs the admitted requests (at most budget / slots bytes) into one
+//     batch as soon as one of the in-flight slots is free, and launches it (descriptor upload, plan and
 //     persistent batch kernels, status download, completion event) on that
 //     slot's stream -- so requests that arrive while earlier batches run are
 //     admitted as slots and budget free up, and consecutive batches overlap
@@ -159,11 +159,17 @@ bool dispatch_locked(Server *s, int sms) {
     int n = 0;
     size_t bytes = 0;
     unsigned long long blocks = 0;
+    // one batch takes at most its share of the budget, so that under load
+    // several batches are queued on the device and the next one is already
+    // there when one finishes (a single request larger than the share still
+    // goes alone)
+    const size_t share = s->budget / s->slots.size();
     while (!s->pending.empty() && n < s->max_batch) {
         Req &r = *s->find(s->pending.front());
         if (r.arrival > t) break;                          // not arrived yet
         const size_t need = 2 * r.nbytes;
         if (s->inflight + bytes + need > s->budget) break;  // FIFO: wait for budget
+        if (n > 0 && bytes + need > share) break;
         const int nr = s->key_nr[r.key_id];
         aes_desc &d = sl->h_desc[n];
         d.rk = (r.dir == 0 ? s->d_rk_enc : s->d_rk_dec) + static_cast<size_t>(r.key_id) * kRkStrideWords;
@@ -225,7 +231,7 @@ void worker_main(Server *s) {
         if (launched) continue;
         if (any_busy) {
             // poll the slots' events again shortly (host side, bounded)
-            s->cv_work.wait_for(lk, std::chrono::microseconds(20));
+            s->cv_work.wait_for(lk, std::chrono::microseconds(10));
         } else if (!s->pending.empty()) {
             const double wait = s->find(s->pending.front())->arrival - now_s();
             if (wait > 0)
@@ -349,19 +355,25 @@ int aes_srv_submit_many(aes_server *h, int n, const int32_t *key_ids, const int3
         return AES_E_ARG;
     const double t0 = now_s();
     int first_err = AES_OK;
-    {
-        std::lock_guard<std::mutex> lk(s->mu);
-        for (int i = 0; i < n; ++i) {
-            const double arr = t0 + (arrival_offsets_s ? arrival_offsets_s[i] : 0.0);
-            const int st = submit_locked(s, key_ids[i], dirs[i], reinterpret_cast<const uint8_t *>(in_devs[i]),
-                                         reinterpret_cast<uint8_t *>(out_devs[i]), nbytes[i], arr, &tickets[i]);
-            if (st != AES_OK) {
-                tickets[i] = 0;
-                if (first_err == AES_OK) first_err = st;
+    // in slices, releasing the lock in between, so that the dispatcher starts
+    // on the first requests while the rest are still being queued
+    constexpr int kSlice = 1024;
+    for (int lo = 0; lo < n; lo += kSlice) {
+        const int hi = n - lo < kSlice ? n : lo + kSlice;
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            for (int i = lo; i < hi; ++i) {
+                const double arr = t0 + (arrival_offsets_s ? arrival_offsets_s[i] : 0.0);
+                const int st = submit_locked(s, key_ids[i], dirs[i], reinterpret_cast<const uint8_t *>(in_devs[i]),
+                                             reinterpret_cast<uint8_t *>(out_devs[i]), nbytes[i], arr, &tickets[i]);
+                if (st != AES_OK) {
+                    tickets[i] = 0;
+                    if (first_err == AES_OK) first_err = st;
+                }
             }
         }
+        s->cv_work.notify_one();
     }
-    s->cv_work.notify_one();
     return first_err;
 }
 

@@ -163,3 +163,14 @@ def test_host_buffer_pipeline(orc, pinned):
     assert np.array_equal(h_out.numpy(), data)
     with pytest.raises(aesgb.AesError):
         aesgb.aes_ecb_host(0, enc, nr, h_in, h_out, n, stage, 32, s)          # staging too small
+
+
+def test_lookup_rate_calibration():
+    torch = torch_cuda()
+    sms = aesgb.aes_device_sm_count(0)
+    sink = torch.zeros(sms * 4096, dtype=torch.uint8, device="cuda")
+    n, t = aesgb.aes_calibrate_lookup_rate(sink, sink.numel())
+    rate = n / t / sms                       # lookups per second per SM
+    assert 1e9 < rate < 32 * 3.0e9           # below 32 per clock at any plausible clock
+    with pytest.raises(aesgb.AesError):
+        aesgb.aes_calibrate_lookup_rate(sink, 16)
