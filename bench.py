@@ -123,6 +123,17 @@ class Dist:
             self.pg.destroy_process_group()
 
 
+def aggregate_throughput(dist: "Dist", local_ms: float, local_bits: float, steps: int):
+    """Whole-job numbers of a weak-scaling run: every rank processed its own
+    shard (`local_bits` per step, no data exchanged); the job's time is the
+    slowest rank's, its work the sum over ranks.  Returns (ms_per_step,
+    Gbit/s of the whole job)."""
+    max_ms = dist.max(local_ms)
+    bits = dist.sum(local_bits)
+    ms_per_step = max_ms / steps
+    return ms_per_step, bits / (ms_per_step / 1e3) / 1e9
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -627,11 +638,8 @@ def run_gb300(args, dist: Dist):
     if not torch.equal(back, pt):
         raise SystemExit("bench: decrypt(encrypt(x)) != x after the timed steps")
 
-    max_ms = dist.max(total_ms)
-    ms_per_step = max_ms / K
     world = dist.world
-    bits_per_step = 2 * nbytes * 8 * world
-    value = bits_per_step / (ms_per_step / 1e3) / 1e9
+    ms_per_step, value = aggregate_throughput(dist, total_ms, 2 * nbytes * 8, K)
     clk = clocks.summary()
 
     # --- roofline of the encryption kernel --------------------------------

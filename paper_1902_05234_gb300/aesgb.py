@@ -13,6 +13,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import sys
 import threading
 
 import numpy as np
@@ -178,12 +179,11 @@ def _ptr(x) -> int:
 
 def _stream(s) -> int:
     if s is None:
-        try:
-            import torch
-            if torch.cuda.is_available() and torch.cuda.is_initialized():
-                return int(torch.cuda.current_stream().cuda_stream)
-        except Exception:  # pragma: no cover - torch absent
-            pass
+        torch = sys.modules.get("torch")
+        if torch is not None and torch.cuda.is_initialized():
+            # the raw handle of torch's current stream, without building a
+            # Stream object (that costs several microseconds per call)
+            return int(torch._C._cuda_getCurrentRawStream(torch._C._cuda_getDevice()))
         return 0
     if isinstance(s, int):
         return s

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <mutex>
 #include <map>
+#include <tuple>
 #include <utility>
 
 #include "aesgb.h"
@@ -25,6 +26,10 @@ constexpr int kMaxDevices = 64;
 std::atomic<int> g_sm_count[kMaxDevices];
 std::mutex g_attr_mu;
 std::map<std::pair<const void *, int>, uint32_t> g_attr_bytes;  // (kernel, device) -> bytes allowed
+// resident CTAs per SM, by (kernel, device, threads, shared bytes): the
+// occupancy query costs microseconds, more than a small launch
+std::mutex g_occ_mu;
+std::map<std::tuple<const void *, int, int, uint32_t>, int> g_occ;
 }  // namespace
 
 int current_device(int *dev) {
@@ -97,9 +102,18 @@ int persistent_grid(const void *fn, int dev, const aes_launch_cfg &c, uint32_t s
     const int sms = sm_count(dev);
     if (sms < 0) return sms;
     int fit = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, fn, c.threads, smem) != cudaSuccess) {
-        (void)cudaGetLastError();
-        return AES_E_CUDA;
+    {
+        std::lock_guard<std::mutex> lk(g_occ_mu);
+        auto it = g_occ.find(std::make_tuple(fn, dev, static_cast<int>(c.threads), smem));
+        if (it != g_occ.end()) fit = it->second;
+    }
+    if (fit == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, fn, c.threads, smem) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return AES_E_CUDA;
+        }
+        std::lock_guard<std::mutex> lk(g_occ_mu);
+        g_occ[std::make_tuple(fn, dev, static_cast<int>(c.threads), smem)] = fit;
     }
     if (fit <= 0) return AES_E_CONFIG;
     const int per_sm = c.ctas_per_sm > 0 && c.ctas_per_sm < fit ? c.ctas_per_sm : fit;
