@@ -61,6 +61,7 @@ def parse_args():
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-served", action="store_true")
     p.add_argument("--no-tune", action="store_true")
+    p.add_argument("--no-stress", action="store_true")
     p.add_argument("--served-requests", type=int, default=20000)
     p.add_argument("--batch-n", type=int, default=4096, help="messages in the batched workload")
     p.add_argument("--batch-max-bytes", type=int, default=16 * MIB, help="largest message of the batched workload")
@@ -491,8 +492,8 @@ def run_served(torch, aesgb, dev, n_req=20000, loads=(0.1, 0.2, 0.3, 0.4, 0.5, 0
 
         run(None)                                   # warm-up (tuned configuration, first launches)
         ref = dst.clone()
-        lat, _, span = run(None)                    # saturated: every request at once
-        peak_bps = total / span
+        # saturated: every request at once; the peak is the best of three
+        peak_bps = max(total / run(None)[2] for _ in range(3))
         rows = []
         identical = bool(torch.equal(dst, ref))
         mean_size = float(np.mean(sizes))
@@ -572,6 +573,52 @@ def run_study(args):
                      "same_output": bool(torch.equal(y, ref))})
     print(json.dumps({"study": "AES-128 ECB encryption, table placement x granularity",
                       "bytes": nbytes, "rows": rows}), flush=True)
+
+
+def run_stress(torch, aesgb, dev, total=16 * GIB, region=64 * MIB, iters=3):
+    """Stress workload: AES-256 ECB decryption in place over 16 GiB of 64 MiB
+    regions cycling uniform random / all-zero / one 16-byte block repeated.
+    Timed as one launch per pass; afterwards every all-zero and periodic region
+    must hold one repeated block (ECB's identical-block invariant), checked on
+    the device."""
+    import numpy as np
+    from paper_1902_05234_gb300 import workloads as wl
+    kinds = wl.stress_region_kinds(total, region)
+    buf = torch.empty(total, dtype=torch.uint8, device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(wl.BASE_SEED + 110)
+    hg = wl.rng(110)
+    for r, kind in enumerate(kinds.tolist()):
+        sl = buf[r * region:(r + 1) * region]
+        if kind == 0:
+            sl.random_(0, 256, generator=g)
+        elif kind == 1:
+            sl.zero_()
+        else:
+            blk = torch.from_numpy(hg.integers(0, 256, 16, dtype=np.uint8)).to(dev)
+            sl.view(-1, 16).copy_(blk.expand(region // 16, 16))
+    _, dec, nr = aesgb.aes_expand_key(256, wl.random_key(256, 110).tobytes())
+    n = total // 16
+    aesgb.aes_ecb_decrypt(dec, nr, buf, buf, n)            # warm-up pass (also in place)
+    torch.cuda.synchronize()
+    s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s_.record()
+    for _ in range(iters):
+        aesgb.aes_ecb_decrypt(dec, nr, buf, buf, n)
+    e_.record()
+    e_.synchronize()
+    ms = s_.elapsed_time(e_) / iters
+    ok = True
+    for r, kind in enumerate(kinds.tolist()):
+        if kind:
+            blocks = buf[r * region:(r + 1) * region].view(-1, 16)
+            ok = ok and bool((blocks == blocks[0]).all())
+    del buf
+    torch.cuda.empty_cache()
+    return {"workload": "AES-256 ECB decrypt in place, 16 GiB of 64 MiB regions: uniform / all-zero / "
+                        "16-byte periodic", "ms": round(ms, 3), "gbps": round(total * 8 / ms / 1e6, 1),
+            "identical_block_invariant": ok,
+            "cfg": repr(aesgb.aes_ecb_get_cfg(1, nr, n))}
 
 
 def run_gb300(args, dist: Dist):
@@ -669,6 +716,10 @@ def run_gb300(args, dist: Dist):
         "peak_basis": f"{sms} SMs x {f_mhz:.0f} MHz (median sampled under load) x 128 B/clk shared-memory "
                       f"lookups (derived from unit counts and the measured clock)",
         "achieved_gbps": round(enc_gbps, 1), "peak_gbps": round(peak_gbps_metric, 1),
+        # the same data pipe also carries the 128-bit global loads and stores:
+        # 64*Nr bytes of lookups + 32 bytes of I/O per block at 128 B/clk/SM
+        "l1tex_bound_gbps": round(sms * f_mhz * 1e6 * 128 / (64 * nr + 32) * 128 / 1e9, 1),
+        "l1tex_frac": round(enc_gbps / (sms * f_mhz * 1e6 * 128 / (64 * nr + 32) * 128 / 1e9), 4),
         "measured_peak": {"gbs": round(measured_lookup_gbs, 1),
                           "lookups_per_clk_per_sm": round(cal_lookups / cal_s / (sms * f_mhz * 1e6), 3),
                           "frac": round(achieved_gbs / measured_lookup_gbs, 4),
@@ -701,6 +752,8 @@ def run_gb300(args, dist: Dist):
     if dist.rank == 0 and world == 1 and not args.no_batched:
         line["batched"] = run_batched(torch, aesgb, dev, n=args.batch_n, tune=not args.no_tune,
                                       hi=args.batch_max_bytes)
+    if dist.rank == 0 and world == 1 and not args.no_stress:
+        line["stress"] = run_stress(torch, aesgb, dev)
     if dist.rank == 0 and world == 1 and not args.no_served:
         line["served"] = run_served(torch, aesgb, dev, n_req=args.served_requests)
     if dist.rank == 0 and world == 1 and not args.no_cpu:
