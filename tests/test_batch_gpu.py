@@ -179,3 +179,36 @@ def test_batch_graph_replay_and_library_workspace(orc):
     b.upload()
     aesgb.aes_ecb_batch(b.desc_dev, b.n)
     check_against_oracle(orc, b, b.output())
+
+
+def test_batch_many_tiny_messages(orc):
+    """20,000 messages of 16..256 bytes: the plan kernel scans 20 tiles of
+    1,024 descriptors and the 32-ary search runs over 20,000 positions."""
+    torch = torch_cuda()
+    g = wl.rng(12)
+    n = 20_000
+    lengths = 16 * g.integers(1, 17, size=n)
+    keybits = g.choice(np.array([128, 192, 256]), size=n)
+    dirs = g.integers(0, 2, size=n)
+    b = DeviceBatch(torch, lengths, keybits, dirs, seed=13)
+    ws, nbytes = b.workspace()
+    status = torch.full((n,), 5, dtype=torch.int32, device="cuda")
+    aesgb.aes_ecb_batch_ws(b.desc_dev, n, ws, nbytes, status)
+    out = b.output()
+    assert bool((status == 0).all())
+    for i in range(0, n, 97):
+        exp = orc.ecb(int(b.dirs[i]), b.keys[i], b.message(b.data, i))
+        assert np.array_equal(b.message(out, i), exp), i
+    # every message against the single-buffer path on the device
+    ref = torch.full_like(b.out_dev, 0x5A)
+    for i in range(0, n, 7):
+        enc, dec, nr = aesgb.aes_expand_key(int(b.keybits[i]), b.keys[i])
+        off = int(b.offsets[i])
+        (aesgb.aes_ecb_encrypt if b.dirs[i] == 0 else aesgb.aes_ecb_decrypt)(
+            enc if b.dirs[i] == 0 else dec, nr, b.in_dev.data_ptr() + off, ref.data_ptr() + off,
+            int(b.lengths[i]) // 16)
+    torch.cuda.synchronize()
+    got = b.out_dev.cpu().numpy()
+    refh = ref.cpu().numpy()
+    for i in range(0, n, 7):
+        assert np.array_equal(b.message(got, i), b.message(refh, i)), i
