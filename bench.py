@@ -552,27 +552,58 @@ def run_study(args):
     ref = torch.empty_like(x)
     enc, _, nr = aesgb.aes_expand_key(128, wl.random_key(128, 100).tobytes())
     rows = []
-    for i, (label, layout, nb, threads) in enumerate(STUDY_VARIANTS):
-        cfg = aesgb.make_cfg(threads, nb, layout, 0)
+    variants = STUDY_VARIANTS + [("constant time: bitsliced, no tables, 32 blocks per thread", None, 32, 256)]
+    for i, (label, layout, nb, threads) in enumerate(variants):
+        if layout is None:
+            cfg = "aes_ecb_crypt_ct(threads=256, 32 blocks/thread)"
+            launch = lambda: aesgb.aes_ecb_crypt_ct(0, enc, nr, x, y, n)  # noqa: E731
+        else:
+            cfg = aesgb.make_cfg(threads, nb, layout, 0)
+            launch = lambda c=cfg: aesgb.aes_ecb_crypt_cfg(0, enc, nr, x, y, n, c)  # noqa: E731
         for _ in range(args.study_warmup):
-            aesgb.aes_ecb_crypt_cfg(0, enc, nr, x, y, n, cfg)
+            launch()
         ms = None
         if args.study_reps > 0:
             s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             s.record()
             for _ in range(args.study_reps):
-                aesgb.aes_ecb_crypt_cfg(0, enc, nr, x, y, n, cfg)
+                launch()
             e.record()
             e.synchronize()
             ms = s.elapsed_time(e) / args.study_reps
         torch.cuda.synchronize()
         if i == 0:
             ref.copy_(y)
-        rows.append({"variant": label, "cfg": repr(cfg), "ms": None if ms is None else round(ms, 4),
+        rows.append({"variant": label, "cfg": cfg if isinstance(cfg, str) else repr(cfg),
+                     "ms": None if ms is None else round(ms, 4),
                      "gbps": None if ms is None else round(nbytes * 8 / ms / 1e6, 1),
                      "same_output": bool(torch.equal(y, ref))})
     print(json.dumps({"study": "AES-128 ECB encryption, table placement x granularity",
                       "bytes": nbytes, "rows": rows}), flush=True)
+
+
+def run_constant_time(torch, aesgb, src, dst, nbytes, key, keybits, iters=5):
+    """The bitsliced (table-free, constant-time) kernel on the same buffer,
+    both directions, checked equal to the T-table kernel's output."""
+    n = nbytes // 16
+    enc, dec, nr = aesgb.aes_expand_key(keybits, key)
+    out = {}
+    ref = torch.empty_like(dst)
+    aesgb.aes_ecb_encrypt(enc, nr, src, ref, n)
+    for d, rk, name in ((0, enc, "enc"), (1, dec, "dec")):
+        a, b = (src, dst) if d == 0 else (ref, dst)
+        aesgb.aes_ecb_crypt_ct(d, rk, nr, a, b, n)
+        s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s_.record()
+        for _ in range(iters):
+            aesgb.aes_ecb_crypt_ct(d, rk, nr, a, b, n)
+        e_.record()
+        e_.synchronize()
+        ms = s_.elapsed_time(e_) / iters
+        same = bool(torch.equal(b, ref if d == 0 else src))
+        out[name] = {"ms": round(ms, 4), "gbps": round(nbytes * 8 / ms / 1e6, 1), "same_as_table_path": same}
+    del ref
+    return {"workload": f"AES-{keybits} ECB, {nbytes // MIB} MiB, bitsliced (no table lookups)", **out}
 
 
 def run_stress(torch, aesgb, dev, total=16 * GIB, region=64 * MIB, iters=3):
@@ -752,6 +783,8 @@ def run_gb300(args, dist: Dist):
     if dist.rank == 0 and world == 1 and not args.no_batched:
         line["batched"] = run_batched(torch, aesgb, dev, n=args.batch_n, tune=not args.no_tune,
                                       hi=args.batch_max_bytes)
+    if dist.rank == 0 and world == 1:
+        line["constant_time"] = run_constant_time(torch, aesgb, pt, ct, nbytes, key, args.keybits)
     if dist.rank == 0 and world == 1 and not args.no_stress:
         line["stress"] = run_stress(torch, aesgb, dev)
     if dist.rank == 0 and world == 1 and not args.no_served:

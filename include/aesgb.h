@@ -277,6 +277,27 @@ int aes_cbc_decrypt(const uint32_t *rk_dec, int nrounds, const uint8_t *iv, cons
 int aes_shutdown(void);
 
 /* ------------------------------------------------------------------------ */
+/* Constant-time ECB (bitsliced)                                             */
+/* ------------------------------------------------------------------------ */
+/* ECB without table lookups, for callers that need the cipher to be free of
+ * data- and key-dependent memory accesses (the side channel behind the
+ * paper's remark on xtime and power analysis, section 3.2.1).  Each thread
+ * transposes 32 blocks into 128 bit planes; SubBytes is a tower-field
+ * GF((2^4)^2) inversion circuit with the affine map, ShiftRows a register
+ * permutation, MixColumns xtime on planes, and round keys enter as mask
+ * planes.  Same results and the same contract as aes_ecb_crypt_cfg: dir 0
+ * encrypt with rk_enc, 1 decrypt with rk_dec (HOST); in/out DEVICE, 16-byte
+ * aligned, equal or disjoint. */
+int aes_ecb_crypt_ct(int dir, const uint32_t *rk, int nrounds, const uint8_t *in, uint8_t *out, size_t nblocks,
+                     void *stream);
+
+/* Test hook: the same bitsliced code run on the host over HOST buffers, so
+ * the circuit can be checked against a reference without a GPU.  Not used by
+ * any other entry point. */
+int aes_ct_selftest_host(int dir, const uint32_t *rk, int nrounds, const uint8_t *in, uint8_t *out,
+                         size_t nblocks);
+
+/* ------------------------------------------------------------------------ */
 /* Serving: continuous batching over the batch kernel                        */
 /* ------------------------------------------------------------------------ */
 /* A request is ECB (eq (1)) of one caller-owned device buffer with a

@@ -107,6 +107,8 @@ _SIGNATURES = {
     "aes_calibrate_lookup_rate": (_i, [_vp, _sz, _vp, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double)]),
     "aes_ecb_host_direct": (_i, [_i, _u32p, _i, _vp, _vp, _sz, _vp]),
+    "aes_ecb_crypt_ct": (_i, [_i, _u32p, _i, _vp, _vp, _sz, _vp]),
+    "aes_ct_selftest_host": (_i, [_i, _u32p, _i, _vp, _vp, _sz]),
     "aes_ctr_crypt": (_i, [_u32p, _i, _u8p, _vp, _vp, _sz, _vp]),
     "aes_cbc_decrypt": (_i, [_u32p, _i, _u8p, _vp, _vp, _sz, _vp]),
     "aes_tune_ecb": (_i, [_i, _i, _u32p, _vp, _vp, _sz, _vp, ctypes.POINTER(aes_launch_cfg)]),
@@ -399,6 +401,22 @@ def aes_ecb_host_direct(direction: int, rk, nrounds: int, host_in, host_out, nbl
     p, _keep = _rk_arg(rk)
     _check(lib().aes_ecb_host_direct(int(direction), p, int(nrounds), _ptr(host_in), _ptr(host_out), int(nblocks),
                                      _stream(stream)), "aes_ecb_host_direct")
+
+
+def aes_ecb_crypt_ct(direction: int, rk, nrounds: int, in_, out, nblocks: int, stream=None) -> None:
+    p, _keep = _rk_arg(rk)
+    _check(lib().aes_ecb_crypt_ct(int(direction), p, int(nrounds), _ptr(in_), _ptr(out), int(nblocks),
+                                  _stream(stream)), "aes_ecb_crypt_ct")
+
+
+def aes_ct_selftest_host(direction: int, rk, nrounds: int, data: np.ndarray) -> np.ndarray:
+    """Run the bitsliced cipher's code on the host (test hook) over host bytes."""
+    p, _keep = _rk_arg(rk)
+    src = np.ascontiguousarray(data, np.uint8)
+    out = np.zeros_like(src)
+    _check(lib().aes_ct_selftest_host(int(direction), p, int(nrounds), src.ctypes.data, out.ctypes.data,
+                                      src.size // 16), "aes_ct_selftest_host")
+    return out
 
 
 def _block16(b):
