@@ -57,28 +57,77 @@ AESGB_CX_HD bsmath::Mat8 mat_of(int id) {
                            : bsmath::kMaps.lin_delta;
 }
 
+// Each map y = M x is evaluated as a straight-line XOR program with shared
+// subexpressions, found at compile time by repeatedly naming the pair of
+// variables that occurs together in the most rows (variable 8 + k =
+// v[a[k]] ^ v[b[k]]); row i is then the XOR of the variables in rows[i].
+struct XorProg {
+    int nnew;
+    int a[24], b[24];
+    uint32_t rows[8];  // bit j: variable j (0..7 inputs, 8.. shared pairs)
+};
+
+AESGB_CX_HD XorProg make_prog(const bsmath::Mat8 &m) {
+    XorProg p{};
+    for (int i = 0; i < 8; ++i) p.rows[i] = m.row[i];
+    int nv = 8;
+    while (p.nnew < 24) {
+        int bi = -1, bj = -1, best = 1;
+        for (int i = 0; i < nv; ++i)
+            for (int j = i + 1; j < nv; ++j) {
+                int cnt = 0;
+                for (int r = 0; r < 8; ++r) cnt += ((p.rows[r] >> i) & 1) && ((p.rows[r] >> j) & 1);
+                if (cnt > best) { best = cnt; bi = i; bj = j; }
+            }
+        if (bi < 0) break;
+        p.a[p.nnew] = bi;
+        p.b[p.nnew] = bj;
+        for (int r = 0; r < 8; ++r)
+            if (((p.rows[r] >> bi) & 1) && ((p.rows[r] >> bj) & 1))
+                p.rows[r] = (p.rows[r] & ~((1u << bi) | (1u << bj))) | (1u << nv);
+        ++nv;
+        ++p.nnew;
+    }
+    return p;
+}
+
+AESGB_CX_HD XorProg prog_of(int id) { return make_prog(mat_of(id)); }
+
+template <int ID, int K = 0>
+AESGB_HD void prog_vars(uint32_t (&v)[32]) {
+    if constexpr (K < prog_of(ID).nnew) {
+        constexpr int ia = prog_of(ID).a[K], ib = prog_of(ID).b[K];
+        v[8 + K] = v[ia] ^ v[ib];
+        prog_vars<ID, K + 1>(v);
+    }
+}
+
 template <int ID, int I, int J = 0>
-AESGB_HD uint32_t row_xor(const uint32_t (&x)[8]) {
-    if constexpr (J == 8) {
+AESGB_HD uint32_t prog_row(const uint32_t (&v)[32]) {
+    if constexpr (J == 32) {
         return 0u;
-    } else if constexpr (((mat_of(ID).row[I] >> J) & 1) != 0) {
-        return x[J] ^ row_xor<ID, I, J + 1>(x);
+    } else if constexpr (((prog_of(ID).rows[I] >> J) & 1) != 0) {
+        return v[J] ^ prog_row<ID, I, J + 1>(v);
     } else {
-        return row_xor<ID, I, J + 1>(x);
+        return prog_row<ID, I, J + 1>(v);
     }
 }
 
 // y = M x + k  (k: mask planes, all-zero or all-one words)
 template <int ID>
 AESGB_HD void matvec(const uint32_t (&x)[8], const uint32_t (&k)[8], uint32_t (&y)[8]) {
-    y[0] = row_xor<ID, 0>(x) ^ k[0];
-    y[1] = row_xor<ID, 1>(x) ^ k[1];
-    y[2] = row_xor<ID, 2>(x) ^ k[2];
-    y[3] = row_xor<ID, 3>(x) ^ k[3];
-    y[4] = row_xor<ID, 4>(x) ^ k[4];
-    y[5] = row_xor<ID, 5>(x) ^ k[5];
-    y[6] = row_xor<ID, 6>(x) ^ k[6];
-    y[7] = row_xor<ID, 7>(x) ^ k[7];
+    uint32_t v[32];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = x[i];
+    prog_vars<ID>(v);
+    y[0] = prog_row<ID, 0>(v) ^ k[0];
+    y[1] = prog_row<ID, 1>(v) ^ k[1];
+    y[2] = prog_row<ID, 2>(v) ^ k[2];
+    y[3] = prog_row<ID, 3>(v) ^ k[3];
+    y[4] = prog_row<ID, 4>(v) ^ k[4];
+    y[5] = prog_row<ID, 5>(v) ^ k[5];
+    y[6] = prog_row<ID, 6>(v) ^ k[6];
+    y[7] = prog_row<ID, 7>(v) ^ k[7];
 }
 
 // ----------------------------------------------------------------- GF(16)
@@ -267,12 +316,36 @@ AESGB_HD void cipher_planes(Planes &s, const RoundMasks *masks, int nr) {
 
 // In-place transpose of a 32x32 bit matrix: afterwards bit j of a[i] is the
 // old bit i of a[j].  Five stages swap blocks of 16, 8, 4, 2, 1 bits between
-// words 16, 8, 4, 2, 1 apart.
+// words 16, 8, 4, 2, 1 apart; the 16- and 8-bit stages are byte permutes.
+AESGB_HD uint32_t byte_perm(uint32_t x, uint32_t y, uint32_t sel) {
+#if defined(__CUDA_ARCH__)
+    return __byte_perm(x, y, sel);
+#else
+    const uint64_t v = (static_cast<uint64_t>(y) << 32) | x;
+    uint32_t r = 0;
+    for (int i = 0; i < 4; ++i) r |= static_cast<uint32_t>((v >> (8 * ((sel >> (4 * i)) & 7))) & 0xFF) << (8 * i);
+    return r;
+#endif
+}
+
 AESGB_HD void transpose32(uint32_t *a) {
-    uint32_t m = 0x0000FFFFu;
-    #pragma unroll
-    for (int s = 16; s > 0; s >>= 1, m ^= (m << s)) {
-        #pragma unroll
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const uint32_t x = a[k], y = a[k + 16];
+        a[k] = byte_perm(x, y, 0x5410u);
+        a[k + 16] = byte_perm(x, y, 0x7632u);
+    }
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        if (k & 8) continue;
+        const uint32_t x = a[k], y = a[k + 8];
+        a[k] = byte_perm(x, y, 0x6240u);
+        a[k + 8] = byte_perm(x, y, 0x7351u);
+    }
+    uint32_t m = 0x0F0F0F0Fu;
+#pragma unroll
+    for (int s = 4; s > 0; s >>= 1, m ^= (m << s)) {
+#pragma unroll
         for (int k = 0; k < 32; ++k) {
             if (k & s) continue;  // k runs over the words whose partner is k + s
             const uint32_t t = ((a[k] >> s) ^ a[k + s]) & m;
