@@ -306,20 +306,34 @@ def run_reference(args, dist: Dist):
 # ---------------------------------------------------------------------------
 
 def timed_ecb(torch, aesgb, rk, nr, direction, src, dst, nblocks, iters=5, warm=2):
-    for _ in range(warm):
-        (aesgb.aes_ecb_encrypt if direction == 0 else aesgb.aes_ecb_decrypt)(rk, nr, src, dst, nblocks)
+    """Device time of one launch.  Small buffers take a few microseconds, less
+    than a Python call, so the launches are captured in a CUDA graph and the
+    replay is timed: the GPU then runs them back to back."""
+    fn = aesgb.aes_ecb_encrypt if direction == 0 else aesgb.aes_ecb_decrypt
+    cap = torch.cuda.Stream()
+    with torch.cuda.stream(cap):
+        for _ in range(warm):
+            fn(rk, nr, src, dst, nblocks, cap)
+    cap.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=cap):
+        for _ in range(iters):
+            fn(rk, nr, src, dst, nblocks, cap)
+    g.replay()
+    torch.cuda.synchronize()
     s = torch.cuda.Event(enable_timing=True)
     e = torch.cuda.Event(enable_timing=True)
     s.record()
-    for _ in range(iters):
-        (aesgb.aes_ecb_encrypt if direction == 0 else aesgb.aes_ecb_decrypt)(rk, nr, src, dst, nblocks)
+    g.replay()
     e.record()
     e.synchronize()
+    del g
     return s.elapsed_time(e) / iters
 
 
-def run_sweep(torch, aesgb, dev):
-    """Single-buffer sweep: 1 MiB .. 4 GiB (powers of 4) x key sizes x directions."""
+def run_sweep(torch, aesgb, dev, tune=True):
+    """Single-buffer sweep: 1 MiB .. 4 GiB (powers of 4) x key sizes x directions,
+    each point tuned first (untimed) as a deployment would."""
     from paper_1902_05234_gb300 import workloads as wl
     sizes = [MIB * 4 ** i for i in range(7)]
     big = sizes[-1]
@@ -334,10 +348,12 @@ def run_sweep(torch, aesgb, dev):
         for d in (0, 1):
             for sz in sizes:
                 n = sz // 16
-                iters = 5 if sz >= 256 * MIB else 20
-                ms = timed_ecb(torch, aesgb, enc if d == 0 else dec, nr, d, src, dst, n, iters=iters)
+                rk = enc if d == 0 else dec
+                cfg = aesgb.aes_tune_ecb(d, nr, rk, src, dst, n) if tune else aesgb.aes_ecb_get_cfg(d, nr, n)
+                iters = 5 if sz >= 256 * MIB else 50
+                ms = timed_ecb(torch, aesgb, rk, nr, d, src, dst, n, iters=iters)
                 rows.append({"keybits": kb, "dir": "enc" if d == 0 else "dec", "bytes": sz,
-                             "ms": round(ms, 4), "gbps": round(sz * 8 / ms / 1e6, 1)})
+                             "ms": round(ms, 4), "gbps": round(sz * 8 / ms / 1e6, 1), "cfg": repr(cfg)})
     del src, dst
     torch.cuda.empty_cache()
     return rows
@@ -782,7 +798,7 @@ def run_gb300(args, dist: Dist):
     del ct, back
     torch.cuda.empty_cache()
     if dist.rank == 0 and world == 1 and not args.no_sweep:
-        line["sweep"] = run_sweep(torch, aesgb, dev)
+        line["sweep"] = run_sweep(torch, aesgb, dev, tune=not args.no_tune)
     if dist.rank == 0 and world == 1 and not args.no_batched:
         line["batched"] = run_batched(torch, aesgb, dev, n=args.batch_n, tune=not args.no_tune,
                                       hi=args.batch_max_bytes)

@@ -306,8 +306,9 @@ int aes_ct_selftest_host(int dir, const uint32_t *rk, int nrounds, const uint8_t
  * request: input and output) stay within mem_budget_bytes, packs what is
  * admitted -- at most mem_budget_bytes / slots per batch, so that several
  * batches queue on the device under load -- into one batch whenever one of
- * `slots` in-flight batch slots is free, and launches it on that slot's stream (descriptor upload, the plan and
- * persistent batch kernels, status download, completion event).  Requests
+ * `slots` in-flight batch slots is free, plans it on the host (requests are
+ * validated at submission) and launches it on that slot's stream (descriptor
+ * and plan upload, the persistent batch kernel, completion event).  Requests
  * that arrive while earlier batches run join the next batch; consecutive
  * batches overlap on the device.  Host waits are bounded; nothing waits on the
  * device.  Latency = host arrival -> host-observed completion.

@@ -415,6 +415,66 @@ int enqueue_batch(const aes_desc *desc, int n, void *ws, size_t ws_bytes, int32_
 }
 
 // ---------------------------------------------------------------------------
+// host-side planning (for callers that know their batch: the server)
+// ---------------------------------------------------------------------------
+// Writes into a HOST buffer of batch_ws_bytes(n) bytes exactly what the plan
+// kernel would write into the workspace for these descriptors, which must all
+// be valid (check_desc): encryptions first in input order, then decryptions;
+// start[] the exclusive prefix of ceil(nblocks / chunk_blocks); counters 0.
+void plan_on_host(const aes_desc *desc, int n, unsigned int chunk_blocks, void *ws_host) {
+    const WsView v = ws_view(ws_host, n);
+    int pos = 0;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int i = 0; i < n; ++i)
+            if ((desc[i].dir == 0) == (pass == 0)) {
+                v.order[pos] = static_cast<uint32_t>(i);
+                v.count[pos] = (desc[i].nblocks + chunk_blocks - 1) / chunk_blocks;
+                ++pos;
+            }
+    unsigned long long run = 0, enc_chunks = 0;
+    for (int p = 0; p < n; ++p) {
+        v.start[p] = run;
+        run += v.count[p];
+        if (desc[v.order[p]].dir == 0) enc_chunks = run;
+    }
+    v.start[n] = run;
+    v.hdr->total_chunks = run;
+    v.hdr->enc_chunks = enc_chunks;
+    v.hdr->next[0] = 0;
+    v.hdr->next[1] = 0;
+    v.hdr->n = static_cast<unsigned int>(n);
+    v.hdr->chunk_blocks = chunk_blocks;
+    v.hdr->n_invalid = 0;
+    v.hdr->pad = 0;
+}
+
+unsigned int batch_chunk_blocks(const aes_batch_cfg &c) {
+    return static_cast<unsigned int>(32 * c.blocks_per_thread * c.chunk_passes);
+}
+
+// The persistent batch kernel alone, on a workspace planned already.
+int enqueue_batch_kernel(const aes_desc *desc, int n, void *ws, const aes_batch_cfg &c, cudaStream_t s) {
+    if (n == 0) return AES_OK;
+    int st = validate_batch_cfg(c);
+    if (st != AES_OK) return st;
+    int dev = 0;
+    if (current_device(&dev) != AES_OK) return AES_E_CUDA;
+    const void *fn = batch_kernel_ptr(c.blocks_per_thread);
+    const uint32_t smem = batch_smem_bytes(c.threads);
+    st = ensure_smem_attr(fn, dev, smem);
+    if (st != AES_OK) return st;
+    const int sms = sm_count(dev);
+    if (sms < 0) return sms;
+    BatchArgs args{desc, ws, n};
+    void *params[] = {&args};
+    if (cudaLaunchKernel(fn, dim3(sms), dim3(c.threads), params, smem, s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return AES_E_CUDA;
+    }
+    return AES_OK;
+}
+
+// ---------------------------------------------------------------------------
 // library-owned workspace for aes_ecb_batch (grown on demand, per device)
 // ---------------------------------------------------------------------------
 namespace {

@@ -7,9 +7,11 @@
 //     output of every admitted, unfinished request) stay within the budget;
 //     a request that does not fit waits, and so do the ones behind it (FIFO);
 //   * packs the admitted requests (at most budget / slots bytes) into one
-//     batch as soon as one of the in-flight slots is free, and launches it (descriptor upload, plan and
-//     persistent batch kernels, status download, completion event) on that
-//     slot's stream -- so requests that arrive while earlier batches run are
+//     batch as soon as one of the in-flight slots is free, plans it on the
+//     host (order and chunk prefix; the requests were validated at
+//     submission) and launches it (descriptor and plan upload, the persistent
+//     batch kernel, completion event) on that slot's stream -- so requests
+//     that arrive while earlier batches run are
 //     admitted as slots and budget free up, and consecutive batches overlap
 //     on the device;
 //   * retires a slot when its event has completed: the requests' statuses and
@@ -57,8 +59,7 @@ struct Slot {
     cudaEvent_t ev = nullptr;
     aes_desc *h_desc = nullptr;
     aes_desc *d_desc = nullptr;
-    int32_t *h_status = nullptr;
-    int32_t *d_status = nullptr;
+    void *h_ws = nullptr;  // page-locked: the batch plan built on the host
     void *d_ws = nullptr;
     size_t ws_bytes = 0;
     bool busy = false;
@@ -97,9 +98,8 @@ void free_server(Server *s) {
         if (sl.ev) cudaEventDestroy(sl.ev);
         if (sl.stream) cudaStreamDestroy(sl.stream);
         if (sl.h_desc) cudaFreeHost(sl.h_desc);
-        if (sl.h_status) cudaFreeHost(sl.h_status);
+        if (sl.h_ws) cudaFreeHost(sl.h_ws);
         if (sl.d_desc) cudaFree(sl.d_desc);
-        if (sl.d_status) cudaFree(sl.d_status);
         if (sl.d_ws) cudaFree(sl.d_ws);
     }
     if (s->d_rk_enc) cudaFree(s->d_rk_enc);
@@ -136,7 +136,7 @@ void retire_locked(Server *s) {
             Req &r = *rp;
             r.done = true;
             r.done_t = t;
-            r.status = ok ? sl.h_status[i] : AES_E_CUDA;
+            r.status = ok ? AES_OK : AES_E_CUDA;  // requests were validated at submission
             s->n_completed++;
             s->bytes_completed += r.nbytes;
             s->last_done = t;
@@ -186,17 +186,20 @@ bool dispatch_locked(Server *s, int sms) {
         ++n;
     }
     if (n == 0) return false;
+    // the plan (message order, chunk prefix, zeroed counters) is built here on
+    // the host -- every request was validated at submission -- and uploaded
+    // with the descriptors, so only the persistent kernel runs on the device
     const aes_batch_cfg cfg = serve_cfg(sms, blocks);
+    plan_on_host(sl->h_desc, n, batch_chunk_blocks(cfg), sl->h_ws);
     bool ok = cudaMemcpyAsync(sl->d_desc, sl->h_desc, sizeof(aes_desc) * n, cudaMemcpyHostToDevice,
                               sl->stream) == cudaSuccess;
-    ok = ok && aes_ecb_batch_ws(sl->d_desc, n, sl->d_ws, sl->ws_bytes, sl->d_status, &cfg, sl->stream) == AES_OK;
-    ok = ok && cudaMemcpyAsync(sl->h_status, sl->d_status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost,
-                               sl->stream) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(sl->d_ws, sl->h_ws, batch_ws_bytes(n), cudaMemcpyHostToDevice, sl->stream) ==
+                   cudaSuccess;
+    ok = ok && enqueue_batch_kernel(sl->d_desc, n, sl->d_ws, cfg, sl->stream) == AES_OK;
     ok = ok && cudaEventRecord(sl->ev, sl->stream) == cudaSuccess;
     if (!ok) {
         (void)cudaGetLastError();
         s->worker_error = AES_E_CUDA;
-        for (int i = 0; i < n; ++i) sl->h_status[i] = AES_E_CUDA;
         // the event may not have been recorded: mark the batch done now
         for (size_t i = 0; i < sl->tickets.size(); ++i) {
             Req &r = *s->find(sl->tickets[i]);
@@ -273,9 +276,8 @@ int aes_srv_create(size_t mem_budget_bytes, int max_keys, int max_batch, int slo
         ok = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) == cudaSuccess &&
              cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) == cudaSuccess &&
              cudaMallocHost(&sl.h_desc, sizeof(aes_desc) * max_batch) == cudaSuccess &&
-             cudaMallocHost(&sl.h_status, sizeof(int32_t) * max_batch) == cudaSuccess &&
+             cudaMallocHost(&sl.h_ws, sl.ws_bytes) == cudaSuccess &&
              cudaMalloc(&sl.d_desc, sizeof(aes_desc) * max_batch) == cudaSuccess &&
-             cudaMalloc(&sl.d_status, sizeof(int32_t) * max_batch) == cudaSuccess &&
              cudaMalloc(&sl.d_ws, sl.ws_bytes) == cudaSuccess;
         sl.tickets.reserve(static_cast<size_t>(max_batch));
     }

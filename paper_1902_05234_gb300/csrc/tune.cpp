@@ -191,7 +191,8 @@ int aes_tune_ecb(int dir, int nrounds, const uint32_t *rk, const uint8_t *in, ui
                 cands.push_back(aes_launch_cfg{th, nb, layout, 0});
             }
     cands.push_back(default_cfg(dir, nrounds, nblocks));
-    const int reps = nblocks >= (size_t(1) << 24) ? 2 : 5;
+    // enough launches that small sizes are timed over tens of microseconds
+    const int reps = nblocks >= (size_t(1) << 24) ? 2 : (nblocks >= (size_t(1) << 18) ? 5 : 20);
     float best_ms = 1e30f;
     aes_launch_cfg best_cfg = cands.back();
     for (const auto &c : cands) {
