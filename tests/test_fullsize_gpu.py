@@ -1,6 +1,7 @@
-"""Parity at the full workload sizes, in the launch configuration the benchmark
-times (the library's default for the size): sampled windows checked against
-the oracle, properties checked over the whole buffer on the device.
+"""Parity at the full workload sizes, in the launch configurations the
+benchmark times: the library's default for the size and every candidate the
+autotuner can pick (the benchmark tunes before timing).  Sampled windows are
+checked against the oracle, properties over the whole buffer on the device.
 
 * single buffers of 4 GiB, AES-128/192/256: 10 windows of 256 KiB (first, last,
   eight seeded random) against the oracle; decrypt(encrypt(x)) == x over all
@@ -13,6 +14,9 @@ the oracle, properties checked over the whole buffer on the device.
   (region boundaries included) against the oracle, and every all-zero or
   periodic region decrypted to one repeated block equal to the oracle's
   decryption of that block (ECB's identical-block invariant).
+* 1 GiB, AES-128 (the benchmark's workload): every tuner candidate gives the
+  same ciphertext (checked against the oracle on windows) and decrypts it back;
+  every batch-tuner candidate gives the same 5.2 GB batch output.
 """
 import numpy as np
 import pytest
@@ -91,7 +95,6 @@ def test_batch_4096_messages_fullsize(orc):
     torch.cuda.synchronize()
     assert bool((status == 0).all())
     assert torch.equal(dst, ref)
-    host_src = None
     for i in range(n):
         ln = int(lengths[i])
         o = int(offs[i])
@@ -105,7 +108,6 @@ def test_batch_4096_messages_fullsize(orc):
             m = src[s:s + w].cpu().numpy()
             exp = orc.ecb(int(dirs[i]), keys[i], m, nthreads=1)
             assert np.array_equal(dst[s:s + w].cpu().numpy(), exp), i
-    del host_src
 
 
 def test_stress_16gib_aes256_decrypt_in_place(orc):
@@ -149,3 +151,84 @@ def test_stress_16gib_aes256_decrypt_in_place(orc):
         exp = zero_pt if kind == 1 else orc.ecb(1, key, period_blocks[r])
         assert np.array_equal(first, exp), f"region {r}"
         assert bool((blocks == blocks[0]).all()), f"region {r} not a single repeated block"
+
+
+def _tuner_candidates():
+    """The configurations aes_tune_ecb chooses among (tune.cpp)."""
+    out = []
+    for layout in (aesgb.LAYOUT_R4, aesgb.LAYOUT_R1):
+        for nb in (1, 2, 4):
+            for th in (128, 256, 512, 768, 1024):
+                if th > (512 if nb >= 4 else 1024):
+                    continue
+                out.append(aesgb.make_cfg(th, nb, layout, 0))
+    out.append(aesgb.aes_ecb_get_cfg(0, 10, (1 << 30) // 16))
+    return out
+
+
+def test_1gib_every_tuner_candidate(orc):
+    """The benchmark tunes before it times, so whichever candidate wins is the
+    timed configuration: all of them give the same 1 GiB ciphertext, which is
+    checked against the oracle on windows, and all decrypt it back."""
+    torch = torch_cuda()
+    nbytes = 1 << 30
+    n = nbytes // 16
+    x = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    _fill_random(torch, x, 60)
+    key = wl.random_key(128, 60).tobytes()
+    enc, dec, nr = aesgb.aes_expand_key(128, key)
+    ref = torch.empty_like(x)
+    aesgb.aes_ecb_encrypt(enc, nr, x, ref, n)
+    torch.cuda.synchronize()
+    win = 128 * 1024
+    for s in (0, nbytes // 3 // 16 * 16, nbytes - win):
+        assert np.array_equal(ref[s:s + win].cpu().numpy(), orc.ecb(0, key, x[s:s + win].cpu().numpy(),
+                                                                   nthreads=16)), s
+    y = torch.empty_like(x)
+    for cfg in _tuner_candidates():
+        aesgb.aes_ecb_crypt_cfg(0, enc, nr, x, y, n, cfg)
+        torch.cuda.synchronize()
+        assert torch.equal(y, ref), repr(cfg)
+        aesgb.aes_ecb_crypt_cfg(1, dec, nr, y, y, n, cfg)
+        torch.cuda.synchronize()
+        assert torch.equal(y, x), repr(cfg)
+
+
+def test_batch_every_tuner_candidate_fullsize():
+    """Every batch configuration aes_tune_batch can choose gives the same
+    output on the 4,096-message workload (5.2 GB)."""
+    torch = torch_cuda()
+    n = 4096
+    lengths, keybits, dirs = wl.batch_workload(n)
+    offs = np.zeros(n + 1, np.int64)
+    np.cumsum(lengths, out=offs[1:])
+    total = int(offs[-1])
+    src = torch.empty(total, dtype=torch.uint8, device="cuda")
+    _fill_random(torch, src, 61)
+    dst = torch.empty_like(src)
+    ref = torch.empty_like(src)
+    g = wl.rng(61)
+    rks = np.zeros((n, 64), np.uint32)
+    nrs = np.zeros(n, np.int64)
+    for i in range(n):
+        key = g.integers(0, 256, int(keybits[i]) // 8, dtype=np.uint8).tobytes()
+        enc, dec, nr = aesgb.aes_expand_key(int(keybits[i]), key)
+        rks[i, :60] = enc if dirs[i] == 0 else dec
+        nrs[i] = nr
+        a, b = src.data_ptr() + int(offs[i]), ref.data_ptr() + int(offs[i])
+        (aesgb.aes_ecb_encrypt if dirs[i] == 0 else aesgb.aes_ecb_decrypt)(rks[i, :60], nr, a, b,
+                                                                         int(lengths[i]) // 16)
+    rk_dev = torch.from_numpy(rks.view(np.uint8).reshape(-1)).cuda()
+    table = aesgb.pack_descs(rk_dev.data_ptr() + 256 * np.arange(n, dtype=np.uint64),
+                             src.data_ptr() + offs[:-1].astype(np.uint64),
+                             dst.data_ptr() + offs[:-1].astype(np.uint64), lengths // 16, nrs, dirs)
+    desc = torch.from_numpy(table.view(np.uint8).copy()).cuda()
+    ws_bytes = aesgb.aes_batch_workspace_bytes(n)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+    for nb in (1, 2):
+        for th in (256, 384, 512):
+            for passes in (8, 16, 32, 64):
+                dst.fill_(0x5A)
+                aesgb.aes_ecb_batch_ws(desc, n, ws, ws_bytes, cfg=aesgb.make_batch_cfg(th, nb, passes, 1))
+                torch.cuda.synchronize()
+                assert torch.equal(dst, ref), (nb, th, passes)
