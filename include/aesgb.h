@@ -26,6 +26,14 @@
  *  - Round keys are the FIPS-197 expanded key as a byte string: word i of
  *    rk holds bytes 4i..4i+3 of that string in memory order, so the layout is
  *    the same on any host.
+ *  - CUDA graphs: the first launch of a kernel configuration on a device sets
+ *    the kernel's shared-memory limit and caches its occupancy (host calls,
+ *    not stream work).  Make one call of each configuration before capturing
+ *    the enqueuing calls into a graph; after that they only enqueue kernels.
+ *    aes_batch_graph_create does this set-up itself.
+ *  - Thread safety: calls may come from several host threads on distinct
+ *    streams; library state (caches, tuned configurations, internal streams)
+ *    is guarded.  A server handle is the exception (see aes_srv_create).
  */
 #ifndef AESGB_H
 #define AESGB_H

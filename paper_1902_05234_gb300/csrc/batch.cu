@@ -609,6 +609,13 @@ int aes_batch_graph_create(const aes_desc *desc_dev, int n, void *ws, size_t ws_
     if (!out || n <= 0) return AES_E_ARG;
     *out = nullptr;
     const aes_batch_cfg c = cfg ? *cfg : batch_cfg_for(n);
+    int st0 = validate_batch_cfg(c);
+    if (st0 != AES_OK) return st0;
+    // one-time per-kernel set-up (shared-memory attribute) before capturing
+    int dev = 0;
+    if (current_device(&dev) != AES_OK) return AES_E_CUDA;
+    st0 = ensure_smem_attr(batch_kernel_ptr(c.blocks_per_thread), dev, batch_smem_bytes(c.threads));
+    if (st0 != AES_OK) return st0;
     cudaStream_t s = nullptr;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return AES_E_CUDA;
     BatchGraph *g = new BatchGraph();
