@@ -247,6 +247,30 @@ def oracle_rate(o, nthreads: int) -> float:
     return data.size / max(time.perf_counter() - t, 1e-6)
 
 
+def openssl_speed():
+    """Context only: OpenSSL's AES-128-ECB (hardware AES instructions) on one
+    host core, if the openssl program exists on this host."""
+    import shutil
+    exe = shutil.which("openssl")
+    if not exe:
+        return None
+    try:
+        r = subprocess.run([exe, "speed", "-elapsed", "-seconds", "1", "-evp", "aes-128-ecb"],
+                           capture_output=True, text=True, timeout=60)
+    except (OSError, subprocess.TimeoutExpired):
+        return None
+    for line in r.stdout.splitlines()[::-1]:
+        parts = line.split()
+        if parts and parts[0].lower().startswith("aes-128"):
+            try:
+                kbs = float(parts[-1].rstrip("k"))  # largest block size, 1000s of bytes per second
+            except ValueError:
+                return None
+            return {"gbps_one_core": round(kbs * 1000 * 8 / 1e9, 2), "source": "openssl speed -evp aes-128-ecb",
+                    "note": "context: hardware AES instructions on one host core, not the oracle"}
+    return None
+
+
 def cpu_baseline(keybits: int, seconds: float = 10.0) -> dict:
     """The oracle as it stands, encrypt + decrypt of a seeded sample sized to
     take about `seconds` on all host cores."""
@@ -264,7 +288,13 @@ def cpu_baseline(keybits: int, seconds: float = 10.0) -> dict:
     o.ecb(1, key, ct, nthreads=cores)
     t2 = time.perf_counter()
     gbps = 2 * nbytes * 8 / (t2 - t0) / 1e9
+    # one thread on 1 MiB, for the per-core figure
+    small = data[:MIB]
+    t3 = time.perf_counter()
+    o.ecb(0, key, small, nthreads=1)
+    single = small.size * 8 / (time.perf_counter() - t3) / 1e9
     return {"value": gbps, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_thread_gbps": round(single, 5), "openssl_context": openssl_speed(),
             "sample": f"AES-{keybits} ECB encrypt+decrypt of {nbytes:,} bytes (seeded uniform random), "
                       f"{cores} threads, contiguous split",
             "seconds": round(t2 - t0, 3), "enc_s": round(t1 - t0, 3), "dec_s": round(t2 - t1, 3)}
