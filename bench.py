@@ -631,25 +631,34 @@ def run_study(args):
 
 def run_constant_time(torch, aesgb, src, nbytes, key, keybits, iters=5):
     """The bitsliced (table-free, constant-time) kernel on the same buffer,
-    both directions, checked equal to the T-table kernel's output."""
+    both directions and every key size, checked equal to the T-table
+    kernel's output.  `enc` / `dec` are the run's own key size; `by_key`
+    holds all three (the key of each size is the run's key, cut or
+    extended)."""
     n = nbytes // 16
-    enc, dec, nr = aesgb.aes_expand_key(keybits, key)
-    out = {}
+    out = {"by_key": {}}
     dst = torch.empty_like(src)
     ref = torch.empty_like(src)
-    aesgb.aes_ecb_encrypt(enc, nr, src, ref, n)
-    for d, rk, name in ((0, enc, "enc"), (1, dec, "dec")):
-        a, b = (src, dst) if d == 0 else (ref, dst)
-        aesgb.aes_ecb_crypt_ct(d, rk, nr, a, b, n)
-        s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s_.record()
-        for _ in range(iters):
+    for kb in (128, 192, 256):
+        k = (key * 2)[:kb // 8]
+        enc, dec, nr = aesgb.aes_expand_key(kb, k)
+        aesgb.aes_ecb_encrypt(enc, nr, src, ref, n)
+        res = {}
+        for d, rk, name in ((0, enc, "enc"), (1, dec, "dec")):
+            a, b = (src, dst) if d == 0 else (ref, dst)
             aesgb.aes_ecb_crypt_ct(d, rk, nr, a, b, n)
-        e_.record()
-        e_.synchronize()
-        ms = s_.elapsed_time(e_) / iters
-        same = bool(torch.equal(b, ref if d == 0 else src))
-        out[name] = {"ms": round(ms, 4), "gbps": round(nbytes * 8 / ms / 1e6, 1), "same_as_table_path": same}
+            s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s_.record()
+            for _ in range(iters):
+                aesgb.aes_ecb_crypt_ct(d, rk, nr, a, b, n)
+            e_.record()
+            e_.synchronize()
+            ms = s_.elapsed_time(e_) / iters
+            same = bool(torch.equal(b, ref if d == 0 else src))
+            res[name] = {"ms": round(ms, 4), "gbps": round(nbytes * 8 / ms / 1e6, 1), "same_as_table_path": same}
+        out["by_key"][str(kb)] = res
+        if kb == keybits:
+            out.update(res)
     del ref, dst
     torch.cuda.empty_cache()
     return {"workload": f"AES-{keybits} ECB, {nbytes // MIB} MiB, bitsliced (no table lookups)", **out}

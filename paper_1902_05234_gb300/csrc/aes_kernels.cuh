@@ -255,23 +255,25 @@ template <int DIR, int NR, int NB, int LAYOUT>
 __global__ void __launch_bounds__(max_threads_for_nb(NB), 1)
     ecb_kernel(const __grid_constant__ EcbArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
-    Tab<LAYOUT, DIR>::fill(smem, threadIdx.x, blockDim.x);
-    __syncthreads();
-
     const uint32_t lane = threadIdx.x & 31u;
-    const Tab<LAYOUT, DIR> tab(smem, lane);
-    const ParamKey key{a.rk.w};
     const unsigned long long n = a.nblocks;
     const unsigned long long wpc = blockDim.x >> 5;
     const unsigned long long step = static_cast<unsigned long long>(gridDim.x) * wpc * 32ull * NB;
     unsigned long long base = (blockIdx.x * wpc + (threadIdx.x >> 5)) * 32ull * NB;
 
+    // The first pass's loads are issued before the table fill, so their HBM
+    // latency overlaps it (this is most of a small launch's fixed cost).
     uint4 cur[NB];
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
         const unsigned long long b = base + lane + 32ull * i;
         cur[i] = b < n ? ld_block(a.in + b) : make_uint4(0, 0, 0, 0);
     }
+    Tab<LAYOUT, DIR>::fill(smem, threadIdx.x, blockDim.x);
+    __syncthreads();
+
+    const Tab<LAYOUT, DIR> tab(smem, lane);
+    const ParamKey key{a.rk.w};
     for (; base < n; base += step) {
         uint4 nxt[NB];
 #pragma unroll

@@ -5,9 +5,9 @@
 // contiguous bytes.  The thread transposes its 32 x 128 bits into 128 bit
 // planes, runs the rounds as logic operations on whole planes, transposes
 // back and stores.  No address depends on key or data.  Round keys reach the
-// S-box circuit as mask planes built on the host from the schedule (one
-// input and one output mask byte per byte position and round, see
-// build_masks) and expanded into shared memory at the start of the kernel.
+// circuits as mask planes built on the host from the schedule (one mask byte
+// per byte position and key step, see build_masks) and expanded into shared
+// memory at the start of the kernel.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -19,67 +19,73 @@
 
 namespace aesgb {
 
-constexpr int kCtThreads = 256;  // 128 plane registers + the S-box circuit's temporaries per thread
+constexpr int kCtThreads = 256;  // 128 plane registers + the circuits' temporaries per thread
 
 struct CtArgs {
     const uint4 *in;
     uint4 *out;
     unsigned long long nblocks;
     int nr;
-    uint8_t masks[14][16][2];  // [application][byte q = r + 4c][0 in, 1 out]
+    uint8_t masks[15][16];  // [key step][byte q = r + 4c]
 };
 
-// Mask bytes of every S-box application, in application order.
-//  encryption, application i (round i+1): input  phi^-1(K_i[q])
-//                                         output 63, and K_Nr at the byte's
-//                                         place after ShiftRows in the last
-//  decryption (inverse cipher, FIPS-197 5.3), application i (round Nr-1-i,
-//  applied after InvShiftRows): input  D_in (63 + K_Nr at the byte's place
-//                               before InvShiftRows) in the first,
-//                               D_in 63 after that
-//                               output K_{Nr-1-i}[q]
-// K_r[q] is byte q of round key r of the encryption schedule w.
-void build_masks(int dir, const uint8_t *w, int nr, uint8_t (*m)[16][2]) {
-    using bsmath::apply;
-    using bsmath::kMaps;
-    for (int i = 0; i < nr; ++i)
-        for (int q = 0; q < 16; ++q) {
-            const int r = q & 3, c = q >> 2;
-            if (dir == 0) {
-                m[i][q][0] = apply(kMaps.enc_in, w[16 * i + q]);
-                const int dest = r + 4 * ((c - r + 4) & 3);
-                m[i][q][1] = static_cast<uint8_t>(0x63 ^ (i == nr - 1 ? w[16 * nr + dest] : 0));
-            } else {
-                const int src = r + 4 * ((c - r + 4) & 3);
-                m[i][q][0] = i == 0 ? apply(kMaps.dec_in, static_cast<uint8_t>(0x63 ^ w[16 * nr + src]))
-                                    : kMaps.dec_in_c;
-                m[i][q][1] = w[16 * (nr - 1 - i) + q];
+// Key bytes of steps 0..Nr as the kernel takes them (bitslice.cuh adds step 0
+// to the input and gives step i to the circuits of round i).  K_i is round
+// key i of the encryption schedule w, as a state (byte q = r + 4c is row r,
+// column c); a byte m wanted at an S-box output is passed as mu = OUT^-1 m
+// (bsc::k_mu_enc / k_mu_dec), which the S-box's product chains add for free.
+//   encryption  step 0: K_0.  Round i adds its key at the S-box outputs,
+//               before ShiftRows and MixColumns, together with the S-box's
+//               constant 63: m[q] = 63 + K'_i[r + 4((c - r) mod 4)], where
+//               K'_i = InvMixColumns(K_i) for i < Nr and K_Nr itself (the
+//               last round has no MixColumns); ShiftRows then carries byte
+//               (r, (c - r) mod 4) to (r, c), and MixColumns(K'_i) = K_i.
+//   decryption  (inverse cipher, FIPS-197 5.3): step 0 is K_Nr; round i adds
+//               K_{Nr-i} right after InvSubBytes, m = K_{Nr-i}, and the column
+//               circuit applies InvMixColumns to the sum.
+void build_masks(int dir, const uint32_t *rk, int nr, uint8_t (*out)[16]) {
+    uint8_t w[240];
+    std::memcpy(w, rk, 16 * (nr + 1));
+    if (dir == 1)  // rk is dw: its keys 1..Nr-1 are InvMixColumns(w_r); MixColumns gives w back
+        for (int r = 1; r < nr; ++r)
+            for (int c = 0; c < 4; ++c) {
+                uint32_t col;
+                std::memcpy(&col, w + 16 * r + 4 * c, 4);
+                col = bsmath::mix_column_model(col);
+                std::memcpy(w + 16 * r + 4 * c, &col, 4);
             }
+    std::memcpy(out[0], w + (dir == 0 ? 0 : 16 * nr), 16);
+    for (int i = 1; i <= nr; ++i) {
+        uint8_t m[16];
+        if (dir == 0) {
+            uint8_t k[16];
+            for (int c = 0; c < 4; ++c) {
+                uint32_t col;
+                std::memcpy(&col, w + 16 * i + 4 * c, 4);
+                if (i < nr) col = bsmath::inv_mix_column_model(col);
+                std::memcpy(k + 4 * c, &col, 4);
+            }
+            for (int q = 0; q < 16; ++q) {
+                const int r = q & 3, c = q >> 2;
+                m[q] = static_cast<uint8_t>(0x63 ^ k[r + 4 * ((c - r + 4) & 3)]);
+            }
+        } else {
+            std::memcpy(m, w + 16 * (nr - i), 16);
         }
+        for (int q = 0; q < 16; ++q) out[i][q] = bs::apply_rows(dir == 0 ? bsc::k_mu_enc : bsc::k_mu_dec, m[q]);
+    }
 }
 
-// The encryption schedule w as bytes from either schedule of aes_expand_key:
-// rk_enc is w; rk_dec is dw, whose round keys 1..Nr-1 are InvMixColumns(w_r),
-// so MixColumns gives them back.
-void schedule_bytes(int dir, const uint32_t *rk, int nr, uint8_t *w) {
-    std::memcpy(w, rk, 16 * (nr + 1));
-    if (dir == 0) return;
-    for (int r = 1; r < nr; ++r)
-        for (int c = 0; c < 4; ++c) {
-            uint32_t col;
-            std::memcpy(&col, w + 16 * r + 4 * c, 4);
-            col = bsmath::mix_column_model(col);
-            std::memcpy(w + 16 * r + 4 * c, &col, 4);
-        }
+// Mask byte -> 8 planes, in the state's layout (plane 8r + b of column c).
+AESGB_HD void expand_mask(const uint8_t (*m)[16], int i, bs::RoundMasks *dst) {
+    const int app = i >> 7, p = i & 127, c = p >> 5, rb = p & 31;
+    dst[app].m[c][rb] = ((m[app][(rb >> 3) + 4 * c] >> (rb & 7)) & 1) ? 0xffffffffu : 0u;
 }
 
 template <int DIR>
 __global__ void __launch_bounds__(kCtThreads, 1) ct_kernel(const __grid_constant__ CtArgs a) {
-    __shared__ bs::RoundMasks masks[14];
-    for (int i = threadIdx.x; i < a.nr * 16 * 2 * 8; i += blockDim.x) {
-        const int b = i & 7, io = (i >> 3) & 1, q = (i >> 4) & 15, app = i >> 8;
-        masks[app].m[q][io][b] = ((a.masks[app][q][io] >> b) & 1) ? 0xffffffffu : 0u;
-    }
+    __shared__ bs::RoundMasks masks[15];
+    for (int i = threadIdx.x; i < (a.nr + 1) * 128; i += blockDim.x) expand_mask(a.masks, i, masks);
     __syncthreads();
     const uint32_t lane = threadIdx.x & 31u;
     const unsigned long long wpc = blockDim.x >> 5;
@@ -130,9 +136,7 @@ int aes_ecb_crypt_ct(int dir, const uint32_t *rk, int nrounds, const uint8_t *in
     args.out = reinterpret_cast<uint4 *>(out);
     args.nblocks = nblocks;
     args.nr = nrounds;
-    uint8_t w[240];
-    schedule_bytes(dir, rk, nrounds, w);
-    build_masks(dir, w, nrounds, args.masks);
+    build_masks(dir, rk, nrounds, args.masks);
     int dev = 0;
     if (current_device(&dev) != AES_OK) return AES_E_CUDA;
     const void *fn = dir == 0 ? reinterpret_cast<const void *>(&ct_kernel<0>)
@@ -155,15 +159,10 @@ int aes_ct_selftest_host(int dir, const uint32_t *rk, int nrounds, const uint8_t
     if ((dir != 0 && dir != 1) || !rk || (nblocks && (!in || !out))) return AES_E_ARG;
     int st = check_nrounds(nrounds);
     if (st != AES_OK) return st;
-    uint8_t w[240];
-    uint8_t mb[14][16][2];
-    schedule_bytes(dir, rk, nrounds, w);
-    build_masks(dir, w, nrounds, mb);
-    bs::RoundMasks masks[14];
-    for (int i = 0; i < nrounds; ++i)
-        for (int q = 0; q < 16; ++q)
-            for (int io = 0; io < 2; ++io)
-                for (int b = 0; b < 8; ++b) masks[i].m[q][io][b] = ((mb[i][q][io] >> b) & 1) ? 0xffffffffu : 0u;
+    uint8_t mb[15][16];
+    build_masks(dir, rk, nrounds, mb);
+    static bs::RoundMasks masks[15];  // 7.5 KB: kept off the host stack
+    for (int i = 0; i < (nrounds + 1) * 128; ++i) expand_mask(mb, i, masks);
     for (size_t g = 0; g < nblocks; g += 32) {
         bs::Planes s;
         for (int j = 0; j < 32; ++j) {

@@ -55,21 +55,21 @@ __device__ __forceinline__ void counter_state(unsigned long long hi, unsigned lo
 template <int NR, int NB, int LAYOUT>
 __global__ void __launch_bounds__(max_threads_for_nb(NB), 1) ctr_kernel(const __grid_constant__ CtrArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
-    Tab<LAYOUT, kEncrypt>::fill(smem, threadIdx.x, blockDim.x);
-    __syncthreads();
     const uint32_t lane = threadIdx.x & 31u;
-    const Tab<LAYOUT, kEncrypt> tab(smem, lane);
-    const ParamKey key{a.rk.w};
     const unsigned long long n = a.nblocks;
     const unsigned long long wpc = blockDim.x >> 5;
     const unsigned long long step = static_cast<unsigned long long>(gridDim.x) * wpc * 32ull * NB;
     unsigned long long base = (blockIdx.x * wpc + (threadIdx.x >> 5)) * 32ull * NB;
-    uint4 cur[NB];
+    uint4 cur[NB];  // first pass loaded before the table fill, as in ecb_kernel
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
         const unsigned long long b = base + lane + 32ull * i;
         cur[i] = b < n ? ld_block(a.in + b) : make_uint4(0, 0, 0, 0);
     }
+    Tab<LAYOUT, kEncrypt>::fill(smem, threadIdx.x, blockDim.x);
+    __syncthreads();
+    const Tab<LAYOUT, kEncrypt> tab(smem, lane);
+    const ParamKey key{a.rk.w};
     for (; base < n; base += step) {
         uint4 nxt[NB];
 #pragma unroll
@@ -104,21 +104,21 @@ __device__ __forceinline__ uint4 shfl_from31(uint4 v) {
 template <int NR, int NB, int LAYOUT>
 __global__ void __launch_bounds__(max_threads_for_nb(NB), 1) cbc_dec_kernel(const __grid_constant__ CbcArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
-    Tab<LAYOUT, kDecrypt>::fill(smem, threadIdx.x, blockDim.x);
-    __syncthreads();
     const uint32_t lane = threadIdx.x & 31u;
-    const Tab<LAYOUT, kDecrypt> tab(smem, lane);
-    const ParamKey key{a.rk.w};
     const unsigned long long n = a.nblocks;
     const unsigned long long wpc = blockDim.x >> 5;
     const unsigned long long step = static_cast<unsigned long long>(gridDim.x) * wpc * 32ull * NB;
     unsigned long long base = (blockIdx.x * wpc + (threadIdx.x >> 5)) * 32ull * NB;
-    uint4 cur[NB];
+    uint4 cur[NB];  // first pass loaded before the table fill, as in ecb_kernel
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
         const unsigned long long b = base + lane + 32ull * i;
         cur[i] = b < n ? ld_block(a.in + b) : make_uint4(0, 0, 0, 0);
     }
+    Tab<LAYOUT, kDecrypt>::fill(smem, threadIdx.x, blockDim.x);
+    __syncthreads();
+    const Tab<LAYOUT, kDecrypt> tab(smem, lane);
+    const ParamKey key{a.rk.w};
     for (; base < n; base += step) {
         uint4 nxt[NB];
 #pragma unroll

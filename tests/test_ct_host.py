@@ -1,7 +1,8 @@
 """The constant-time (bitsliced) cipher's code, run on the host through its
 test hook, against the oracle: every key size, both directions, partial
-32-block groups.  The circuit's S-box, inverse S-box and InvMixColumns
-factoring are also checked at compile time (static_asserts)."""
+32-block groups.  The generated circuits (S-box, inverse S-box core and
+output, MixColumns, InvMixColumns with the S-box output map) are also checked
+at compile time (static_asserts in bitslice.cuh)."""
 import numpy as np
 import pytest
 
@@ -29,3 +30,15 @@ def test_bitsliced_host_identical_blocks(orc):
     ct = aesgb.aes_ct_selftest_host(0, enc, nr, data).reshape(-1, 16)
     assert (ct == ct[0]).all()
     assert np.array_equal(ct[0], orc.ecb(0, key, np.zeros(16, np.uint8)))
+
+
+def test_generated_circuits_are_fresh():
+    """bitslice_circuits.h is exactly what gen_bitslice.py writes (the
+    generator also re-verifies every circuit against the S-box, the inverse
+    S-box, MixColumns and InvMixColumns before writing)."""
+    import subprocess
+    import sys
+    from pathlib import Path
+    gen = Path(aesgb.__file__).resolve().parent / "csrc" / "gen_bitslice.py"
+    r = subprocess.run([sys.executable, str(gen), "--check"], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
