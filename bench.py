@@ -664,6 +664,23 @@ def run_constant_time(torch, aesgb, src, nbytes, key, keybits, iters=5):
     return {"workload": f"AES-{keybits} ECB, {nbytes // MIB} MiB, bitsliced (no table lookups)", **out}
 
 
+def ct_roofline(aesgb, ct, nbytes, keybits, sms, f_mhz):
+    """The bitsliced kernel is bound by the integer-logic (ALU) pipe: 64 lanes
+    per clock per SM, one 3-input gate or byte permute per lane.  achieved =
+    the logic operations its circuits spend per block (aes_ct_ops_per_block,
+    counted from the gate tables) x blocks per second; peak = SMs x 64 x the
+    SM clock sampled under load."""
+    nr = nrounds_of(keybits)
+    peak = sms * 64 * f_mhz * 1e6 / 1e12
+    out = {"bound": "alu", "unit": "Tops/s", "peak": round(peak, 2),
+           "peak_basis": f"{sms} SMs x 64 logic lanes/clk x {f_mhz:.0f} MHz (median sampled under load)"}
+    for d, name in ((0, "enc"), (1, "dec")):
+        ops = aesgb.aes_ct_ops_per_block(d, nr)
+        achieved = ops * (nbytes / 16) / (ct[name]["ms"] / 1e3) / 1e12
+        out[name] = {"ops_per_block": round(ops, 2), "achieved": round(achieved, 2), "frac": round(achieved / peak, 4)}
+    return out
+
+
 def run_modes(torch, aesgb, src, nbytes, key, keybits, iters=5):
     """CTR and parallel CBC decryption on the same buffer (same tables and
     round code as ECB, so the same shared-memory lookup bound)."""
@@ -869,6 +886,8 @@ def run_gb300(args, dist: Dist):
         line["modes"] = run_modes(torch, aesgb, pt, nbytes, key, args.keybits)
     if dist.rank == 0 and world == 1 and not args.no_ct:
         line["constant_time"] = run_constant_time(torch, aesgb, pt, nbytes, key, args.keybits)
+        line["constant_time"]["roofline"] = ct_roofline(aesgb, line["constant_time"], nbytes, args.keybits,
+                                                        sms, f_mhz)
     if dist.rank == 0 and world == 1 and not args.no_stress:
         line["stress"] = run_stress(torch, aesgb, dev)
     if dist.rank == 0 and world == 1 and not args.no_served:

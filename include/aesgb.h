@@ -290,14 +290,26 @@ int aes_shutdown(void);
 /* ECB without table lookups, for callers that need the cipher to be free of
  * data- and key-dependent memory accesses (the side channel behind the
  * paper's remark on xtime and power analysis, section 3.2.1).  Each thread
- * transposes 32 blocks into 128 bit planes; SubBytes is a tower-field
- * GF((2^4)^2) inversion circuit with the affine map, ShiftRows a register
- * permutation, MixColumns xtime on planes, and round keys enter as mask
- * planes.  Same results and the same contract as aes_ecb_crypt_cfg: dir 0
- * encrypt with rk_enc, 1 decrypt with rk_dec (HOST); in/out DEVICE, 16-byte
- * aligned, equal or disjoint. */
+ * transposes 32 blocks into 128 bit planes and runs every round as fixed
+ * circuits of 3-input logic gates: a tower-field GF((2^4)^2) inversion
+ * circuit with the affine map for SubBytes, a register permutation for
+ * ShiftRows, a MixColumns circuit (decryption: one circuit per column for
+ * the inverse S-box's output map and InvMixColumns); round keys enter the
+ * S-box circuits as mask planes.  Same results and the same contract as
+ * aes_ecb_crypt_cfg: dir 0 encrypt with rk_enc, 1 decrypt with rk_dec
+ * (HOST); in/out DEVICE, 16-byte aligned, equal or disjoint. */
 int aes_ecb_crypt_ct(int dir, const uint32_t *rk, int nrounds, const uint8_t *in, uint8_t *out, size_t nblocks,
                      void *stream);
+
+/* Logic operations (one 3-input gate or byte permute each, the integer-logic
+ * pipe's unit of work) that aes_ecb_crypt_ct spends per 16-byte block for
+ * direction dir and nrounds rounds, counted from its circuits: the key of
+ * step 0 on the planes, the rounds' S-box, MixColumns / InvMixColumns and
+ * output circuits, and the two in-register 32x32 transposes per column
+ * (their shifts run on the multiply pipe and are not counted).  Host only;
+ * *ops_per_block written on AES_OK; bad dir / nrounds / NULL -> AES_E_ARG /
+ * AES_E_NROUNDS. */
+int aes_ct_ops_per_block(int dir, int nrounds, double *ops_per_block);
 
 /* Test hook: the same bitsliced code run on the host over HOST buffers, so
  * the circuit can be checked against a reference without a GPU.  Not used by

@@ -109,6 +109,7 @@ _SIGNATURES = {
     "aes_ecb_host_direct": (_i, [_i, _u32p, _i, _vp, _vp, _sz, _vp]),
     "aes_ecb_crypt_ct": (_i, [_i, _u32p, _i, _vp, _vp, _sz, _vp]),
     "aes_ct_selftest_host": (_i, [_i, _u32p, _i, _vp, _vp, _sz]),
+    "aes_ct_ops_per_block": (_i, [_i, _i, ctypes.POINTER(ctypes.c_double)]),
     "aes_ctr_crypt": (_i, [_u32p, _i, _u8p, _vp, _vp, _sz, _vp]),
     "aes_cbc_decrypt": (_i, [_u32p, _i, _u8p, _vp, _vp, _sz, _vp]),
     "aes_tune_ecb": (_i, [_i, _i, _u32p, _vp, _vp, _sz, _vp, ctypes.POINTER(aes_launch_cfg)]),
@@ -407,6 +408,13 @@ def aes_ecb_crypt_ct(direction: int, rk, nrounds: int, in_, out, nblocks: int, s
     p, _keep = _rk_arg(rk)
     _check(lib().aes_ecb_crypt_ct(int(direction), p, int(nrounds), _ptr(in_), _ptr(out), int(nblocks),
                                   _stream(stream)), "aes_ecb_crypt_ct")
+
+
+def aes_ct_ops_per_block(direction: int, nrounds: int) -> float:
+    """Logic operations per 16-byte block of the constant-time kernel."""
+    v = ctypes.c_double()
+    _check(lib().aes_ct_ops_per_block(int(direction), int(nrounds), ctypes.byref(v)), "aes_ct_ops_per_block")
+    return v.value
 
 
 def aes_ct_selftest_host(direction: int, rk, nrounds: int, data: np.ndarray) -> np.ndarray:

@@ -154,6 +154,23 @@ int aes_ecb_crypt_ct(int dir, const uint32_t *rk, int nrounds, const uint8_t *in
     return AES_OK;
 }
 
+int aes_ct_ops_per_block(int dir, int nrounds, double *ops_per_block) {
+    if ((dir != 0 && dir != 1) || !ops_per_block) return AES_E_ARG;
+    const int st = check_nrounds(nrounds);
+    if (st != AES_OK) return st;
+    // per thread and 32-block group: 128 planes of step-0 key, the rounds,
+    // 8 transposes of 32 words (stages 16 and 8: one byte permute per word,
+    // stages 4, 2 and 1: one bit-select per word)
+    long long g = 128 + 8 * (2 * 32 + 3 * 32);
+    if (dir == 0)
+        g += 16LL * nrounds * bsc::k_sbox_enc.kGates + 4LL * (nrounds - 1) * bsc::k_mix_columns.kGates;
+    else
+        g += 16LL * nrounds * bsc::k_sbox_core_dec.kGates + 4LL * (nrounds - 1) * bsc::k_inv_mix_out.kGates +
+             16LL * bsc::k_sbox_out_dec.kGates;
+    *ops_per_block = static_cast<double>(g) / 32.0;
+    return AES_OK;
+}
+
 int aes_ct_selftest_host(int dir, const uint32_t *rk, int nrounds, const uint8_t *in, uint8_t *out,
                          size_t nblocks) {
     if ((dir != 0 && dir != 1) || !rk || (nblocks && (!in || !out))) return AES_E_ARG;

@@ -42,3 +42,24 @@ def test_generated_circuits_are_fresh():
     gen = Path(aesgb.__file__).resolve().parent / "csrc" / "gen_bitslice.py"
     r = subprocess.run([sys.executable, str(gen), "--check"], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr
+
+
+def test_ops_per_block_counts_the_circuits():
+    """aes_ct_ops_per_block is the gate count of what one block goes through
+    (the generated tables' sizes, as the header's comments state them)."""
+    import re
+    from pathlib import Path
+    hdr = (Path(aesgb.__file__).resolve().parent / "csrc" / "bitslice_circuits.h").read_text()
+    gates = {name: int(n) for name, n in re.findall(r"// (\w+): \d+ inputs, (\d+) gates", hdr)}
+    assert set(gates) == {"sbox_enc", "sbox_core_dec", "sbox_out_dec", "inv_mix_out", "mix_columns"}
+    fixed = 128 + 8 * 160  # step-0 key planes, 8 transposes of 32 words
+    for nr in (10, 12, 14):
+        enc = fixed + 16 * nr * gates["sbox_enc"] + 4 * (nr - 1) * gates["mix_columns"]
+        dec = (fixed + 16 * nr * gates["sbox_core_dec"] + 4 * (nr - 1) * gates["inv_mix_out"]
+               + 16 * gates["sbox_out_dec"])
+        assert aesgb.aes_ct_ops_per_block(0, nr) == enc / 32
+        assert aesgb.aes_ct_ops_per_block(1, nr) == dec / 32
+    with pytest.raises(aesgb.AesError):
+        aesgb.aes_ct_ops_per_block(0, 11)
+    with pytest.raises(aesgb.AesError):
+        aesgb.aes_ct_ops_per_block(2, 10)
