@@ -495,6 +495,25 @@ def run_batched(torch, aesgb, dev, n=4096, tune=True, hi=16 * MIB):
     return out
 
 
+def batch_roofline(batched, n, hi, sms, f_mhz):
+    """The single-buffer kernel's bounds summed over the batch's messages: a
+    block of a message with Nr rounds moves 64 Nr + 32 bytes through the
+    L1TEX data pipe (16 Nr four-byte lookups, a 16-byte load and store), which
+    serves 128 B per clock per SM; the lookups alone (64 Nr bytes) give the
+    shared-memory bound."""
+    from paper_1902_05234_gb300 import workloads as wl
+    lengths, keybits, _ = wl.batch_workload(n, hi=hi)
+    blocks = lengths.astype(float) / 16
+    nr = keybits.astype(float) / 32 + 6
+    rate = sms * 128 * f_mhz * 1e6  # bytes per second through the pipe
+    bits = float(lengths.sum()) * 8
+    l1 = bits / (float((blocks * (64 * nr + 32)).sum()) / rate) / 1e9
+    smem = bits / (float((blocks * 64 * nr).sum()) / rate) / 1e9
+    return {"bound": "l1tex", "unit": "Gbit/s", "peak": round(l1, 1), "frac": round(batched["gbps"] / l1, 4),
+            "smem_peak": round(smem, 1), "smem_frac": round(batched["gbps"] / smem, 4),
+            "peak_basis": f"{sms} SMs x {f_mhz:.0f} MHz x 128 B/clk over 64 Nr + 32 B per block of each message"}
+
+
 def run_served(torch, aesgb, dev, n_req=20000, loads=(0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9, 1.0)):
     """Served workload: a Poisson stream of encrypt/decrypt requests, sizes
     log-uniform 64 B .. 4 MiB, keys drawn from 1,024 resident schedules,
@@ -882,6 +901,8 @@ def run_gb300(args, dist: Dist):
     if dist.rank == 0 and world == 1 and not args.no_batched:
         line["batched"] = run_batched(torch, aesgb, dev, n=args.batch_n, tune=not args.no_tune,
                                       hi=args.batch_max_bytes)
+        line["batched"]["roofline"] = batch_roofline(line["batched"], args.batch_n, args.batch_max_bytes,
+                                                     sms, f_mhz)
     if dist.rank == 0 and world == 1:
         line["modes"] = run_modes(torch, aesgb, pt, nbytes, key, args.keybits)
     if dist.rank == 0 and world == 1 and not args.no_ct:
