@@ -519,7 +519,8 @@ def run_served(torch, aesgb, dev, n_req=20000, loads=(0.1, 0.2, 0.3, 0.4, 0.5, 0
     log-uniform 64 B .. 4 MiB, keys drawn from 1,024 resident schedules,
     direction 50/50, through the continuous-batching server under a 4 GiB
     device-memory budget.  Peak = the same requests all arriving at once;
-    offered load is then swept as a fraction of that peak."""
+    offered load is then swept as a fraction of that peak.  The peak is set
+    against the same requests as one plain launch each (served_loop_baseline)."""
     import numpy as np
     from paper_1902_05234_gb300 import workloads as wl
     unit_arrivals, sizes, key_ids, dirs = wl.served_workload(n_req, rate_per_s=1.0, n_keys=1024)
@@ -536,9 +537,11 @@ def run_served(torch, aesgb, dev, n_req=20000, loads=(0.1, 0.2, 0.3, 0.4, 0.5, 0
     srv = aesgb.aes_srv_create(4 << 30, 1024, max_batch=8192, slots=4)
     try:
         kg = wl.rng(61)
+        host_keys = []
         for k in range(1024):
             kb = int(kg.choice([128, 192, 256]))
-            aesgb.aes_srv_put_key(srv, k, kb, kg.integers(0, 256, kb // 8, dtype=np.uint8).tobytes())
+            host_keys.append((kb, kg.integers(0, 256, kb // 8, dtype=np.uint8).tobytes()))
+            aesgb.aes_srv_put_key(srv, k, *host_keys[-1])
 
         submit_ms = []
 
@@ -577,16 +580,70 @@ def run_served(torch, aesgb, dev, n_req=20000, loads=(0.1, 0.2, 0.3, 0.4, 0.5, 0
         stats = aesgb.aes_srv_stats(srv)
     finally:
         aesgb.aes_srv_destroy(srv)
+    loop = served_loop_baseline(torch, aesgb, src, ref, offs, sizes, key_ids, dirs, host_keys)
     out = {"workload": f"{n_req} requests per load point, Poisson arrivals, sizes log-uniform 64 B..4 MiB "
                        f"(total {total:,} B), 1,024 resident keys (128/192/256), direction 50/50, "
                        f"4 GiB budget, 4 in-flight batches",
            "peak_gbps": round(peak_bps * 8 / 1e9, 1), "sweep": rows,
            "submit_many_ms": round(statistics.median(submit_ms), 3),
            "identical_across_loads": identical, "batches_total": stats["batches"],
-           "peak_inflight_bytes": stats["peak_inflight_bytes"]}
+           "peak_inflight_bytes": stats["peak_inflight_bytes"],
+           "loop_graph_gbps": loop["graph_gbps"], "loop_python_gbps": loop["python_gbps"],
+           "speedup_vs_loop_graph": round(peak_bps * 8 / 1e9 / loop["graph_gbps"], 3),
+           "speedup_vs_loop_python": round(peak_bps * 8 / 1e9 / loop["python_gbps"], 3),
+           "identical_to_loop": loop["identical"]}
     del src, dst, ref
     torch.cuda.empty_cache()
     return out
+
+
+def served_loop_baseline(torch, aesgb, src, ref, offs, sizes, key_ids, dirs, host_keys):
+    """The served requests as the loop a caller writes without the server: one
+    aes_ecb_encrypt/decrypt launch per request on one stream, schedules
+    expanded on the host beforehand.  Timed as a Python loop (launch overhead
+    included, as the caller would see it) and as a CUDA-graph replay of the
+    same launches (the launch cost taken away); the output must equal the
+    server's."""
+    import numpy as np
+    n = len(sizes)
+    total = int(offs[-1])
+    out = torch.empty_like(src)
+    sched = [aesgb.aes_expand_key(kb, key) for kb, key in host_keys]
+    stream = torch.cuda.current_stream()
+    ins = [src.data_ptr() + int(offs[i]) for i in range(n)]
+    outs = [out.data_ptr() + int(offs[i]) for i in range(n)]
+
+    def launches(strm):
+        for i in range(n):
+            enc, dec, nr = sched[int(key_ids[i])]
+            if dirs[i] == 0:
+                aesgb.aes_ecb_encrypt(enc, nr, ins[i], outs[i], int(sizes[i]) // 16, strm)
+            else:
+                aesgb.aes_ecb_decrypt(dec, nr, ins[i], outs[i], int(sizes[i]) // 16, strm)
+
+    launches(stream)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    launches(stream)
+    torch.cuda.synchronize()
+    py_s = time.perf_counter() - t
+    identical = bool(torch.equal(out, ref))
+    cap = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=cap, capture_error_mode="relaxed"):
+        launches(cap)
+    g.replay()
+    torch.cuda.synchronize()
+    s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s_.record(stream)
+    for _ in range(3):
+        g.replay()
+    e_.record(stream)
+    e_.synchronize()
+    graph_s = s_.elapsed_time(e_) / 3 / 1e3
+    del g, out
+    return {"graph_gbps": round(total * 8 / graph_s / 1e9, 1), "python_gbps": round(total * 8 / py_s / 1e9, 1),
+            "identical": identical}
 
 
 STUDY_VARIANTS = [  # (label, layout, blocks/thread, threads)
