@@ -654,6 +654,8 @@ STUDY_VARIANTS = [  # (label, layout, blocks/thread, threads)
     ("shared, 4 replicated tables, 16 B/thread", 0, 1, 1024),
     ("shared, 4 replicated tables, 32 B/thread", 0, 2, 1024),
     ("shared, 4 replicated tables, 64 B/thread", 0, 4, 512),
+    ("shared, 4 replicated tables, TMA-staged input, 32 B/thread", 4, 2, 1024),
+    ("shared, 4 replicated tables, TMA-staged input, 64 B/thread", 4, 4, 512),
 ]
 
 

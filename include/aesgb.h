@@ -70,6 +70,14 @@ const char *aes_status_str(int status);
 /* Library version, major*10000 + minor*100 + patch. */
 int aes_version(void);
 
+/* Number of bounded device-side waits (the TMA-staged kernel's mbarrier
+ * waits, about one second each) that ran out since the last call, summed
+ * over all launches on the current device; reading resets it.  A timed-out
+ * warp stops without finishing its blocks, so a non-zero count means some
+ * output of those launches is missing.  DEVICE-synchronous (a cudaMemcpy
+ * from the counter). */
+int aes_wait_timeouts(unsigned long long *count);
+
 /* ------------------------------------------------------------------------ */
 /* Key schedule (host)                                                       */
 /* ------------------------------------------------------------------------ */
@@ -118,7 +126,11 @@ typedef enum aes_layout {
                              (enc) / 160 KiB (dec); conflict-free, 1 CTA per SM   */
     AES_LAYOUT_R1 = 1,    /* 1 table per bank-replicated + byte rotations: 64 KiB  */
     AES_LAYOUT_P4 = 2,    /* 4 plain 1 KiB tables in shared memory (bank conflicts) */
-    AES_LAYOUT_CONST = 3  /* tables in constant memory, as in the paper (4.2)      */
+    AES_LAYOUT_CONST = 3, /* tables in constant memory, as in the paper (4.2)      */
+    AES_LAYOUT_R4_TMA = 4 /* R4 tables; the plaintext staged into shared memory by
+                             TMA bulk copies (two 512 x blocks_per_thread-byte
+                             tiles per warp, mbarrier-tracked, two passes ahead)
+                             instead of loaded into registers                     */
 } aes_layout;
 
 /* A launch configuration of the ECB kernels. */

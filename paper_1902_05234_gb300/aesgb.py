@@ -24,8 +24,8 @@ LIB_PATH = os.path.join(_HERE, "libaesgb.so")
 _lib = None
 _lock = threading.Lock()
 
-LAYOUT_R4, LAYOUT_R1, LAYOUT_P4, LAYOUT_CONST = 0, 1, 2, 3
-LAYOUT_NAMES = {0: "R4", 1: "R1", 2: "P4", 3: "CONST"}
+LAYOUT_R4, LAYOUT_R1, LAYOUT_P4, LAYOUT_CONST, LAYOUT_R4_TMA = 0, 1, 2, 3, 4
+LAYOUT_NAMES = {0: "R4", 1: "R1", 2: "P4", 3: "CONST", 4: "R4_TMA"}
 ENCRYPT, DECRYPT = 0, 1
 
 
@@ -110,6 +110,7 @@ _SIGNATURES = {
     "aes_ecb_crypt_ct": (_i, [_i, _u32p, _i, _vp, _vp, _sz, _vp]),
     "aes_ct_selftest_host": (_i, [_i, _u32p, _i, _vp, _vp, _sz]),
     "aes_ct_ops_per_block": (_i, [_i, _i, ctypes.POINTER(ctypes.c_double)]),
+    "aes_wait_timeouts": (_i, [ctypes.POINTER(ctypes.c_ulonglong)]),
     "aes_ctr_crypt": (_i, [_u32p, _i, _u8p, _vp, _vp, _sz, _vp]),
     "aes_cbc_decrypt": (_i, [_u32p, _i, _u8p, _vp, _vp, _sz, _vp]),
     "aes_tune_ecb": (_i, [_i, _i, _u32p, _vp, _vp, _sz, _vp, ctypes.POINTER(aes_launch_cfg)]),
@@ -408,6 +409,13 @@ def aes_ecb_crypt_ct(direction: int, rk, nrounds: int, in_, out, nblocks: int, s
     p, _keep = _rk_arg(rk)
     _check(lib().aes_ecb_crypt_ct(int(direction), p, int(nrounds), _ptr(in_), _ptr(out), int(nblocks),
                                   _stream(stream)), "aes_ecb_crypt_ct")
+
+
+def aes_wait_timeouts() -> int:
+    """Bounded device waits that ran out since the last call (reading resets it)."""
+    v = ctypes.c_ulonglong()
+    _check(lib().aes_wait_timeouts(ctypes.byref(v)), "aes_wait_timeouts")
+    return v.value
 
 
 def aes_ct_ops_per_block(direction: int, nrounds: int) -> float:

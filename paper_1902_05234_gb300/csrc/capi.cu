@@ -82,14 +82,20 @@ void order_round_keys(int dir, const uint32_t *rk, int nr, RoundKeys *out) {
 }
 
 const void *ecb_kernel_ptr(int dir, int nr, int nb, int layout) {
+    if (layout == AES_LAYOUT_R4_TMA) return ecb_kernel_tma(dir, nr, nb);
     return dir == kEncrypt ? ecb_kernel_enc(nr, nb, layout) : ecb_kernel_dec(nr, nb, layout);
+}
+
+uint32_t ecb_smem_bytes(int dir, const aes_launch_cfg &c) {
+    return c.layout == AES_LAYOUT_R4_TMA ? ecb_tma_smem_bytes(dir, c.threads, c.blocks_per_thread)
+                                         : table_smem_bytes(dir, c.layout);
 }
 
 int validate_cfg(const aes_launch_cfg &c) {
     if (c.blocks_per_thread != 1 && c.blocks_per_thread != 2 && c.blocks_per_thread != 4) return AES_E_CONFIG;
     if (c.threads < 32 || c.threads % 32 || c.threads > max_threads_for_nb(c.blocks_per_thread))
         return AES_E_CONFIG;
-    if (c.layout < AES_LAYOUT_R4 || c.layout > AES_LAYOUT_CONST) return AES_E_CONFIG;
+    if (c.layout < AES_LAYOUT_R4 || c.layout > AES_LAYOUT_R4_TMA) return AES_E_CONFIG;
     if (c.ctas_per_sm < 0 || c.ctas_per_sm > 32) return AES_E_CONFIG;
     return AES_OK;
 }
@@ -130,7 +136,7 @@ int launch_ecb(int dir, const uint32_t *rk, int nr, const uint8_t *in, uint8_t *
     if (!fn) return AES_E_CONFIG;
     int dev = 0;
     if (current_device(&dev) != AES_OK) return AES_E_CUDA;
-    const uint32_t smem = table_smem_bytes(dir, c.layout);
+    const uint32_t smem = ecb_smem_bytes(dir, c);
     int st = ensure_smem_attr(fn, dev, smem);
     if (st != AES_OK) return st;
     int grid = 0;
@@ -181,6 +187,11 @@ const char *aes_status_str(int status) {
 }
 
 int aes_version(void) { return 10000; }
+
+int aes_wait_timeouts(unsigned long long *count) {
+    if (!count) return AES_E_ARG;
+    return read_wait_timeouts(count);
+}
 
 int aes_expand_key(int keybits, const uint8_t *key, uint32_t *rk_enc, uint32_t *rk_dec) {
     return expand_key_host(keybits, key, rk_enc, rk_dec);

@@ -10,6 +10,13 @@ namespace aesgb {
 const void *ecb_kernel_enc(int nr, int nb, int layout);
 const void *ecb_kernel_dec(int nr, int nb, int layout);
 
+// ecb_tma.cu: the TMA-staged variant (layout AES_LAYOUT_R4_TMA), its dynamic
+// shared memory (R4 tables, two tiles of 512 nb bytes and two mbarriers per
+// warp), and the count of bounded device waits that ran out (read and reset).
+const void *ecb_kernel_tma(int dir, int nr, int nb);
+uint32_t ecb_tma_smem_bytes(int dir, int threads, int nb);
+int read_wait_timeouts(unsigned long long *count);
+
 // Copy table `which` (0 te0, 1 td0, 2 S-box, 3 InvS) from the constant bank of
 // the encrypt module on the current device.  Returns a cudaError_t value.
 int ecb_module_const_table(int which, uint32_t *out);

@@ -47,8 +47,8 @@ def test_edge_sizes_default_cfg(orc, keybits, direction):
 
 def all_cfgs():
     out = []
-    for layout in (aesgb.LAYOUT_R4, aesgb.LAYOUT_R1, aesgb.LAYOUT_P4, aesgb.LAYOUT_CONST):
-        nbs = (1, 2, 4) if layout in (aesgb.LAYOUT_R4, aesgb.LAYOUT_R1) else (1,)
+    for layout in (aesgb.LAYOUT_R4, aesgb.LAYOUT_R1, aesgb.LAYOUT_P4, aesgb.LAYOUT_CONST, aesgb.LAYOUT_R4_TMA):
+        nbs = (1, 2, 4) if layout in (aesgb.LAYOUT_R4, aesgb.LAYOUT_R1, aesgb.LAYOUT_R4_TMA) else (1,)
         for nb in nbs:
             for threads in (64, 256, 512, 1024):
                 if nb == 4 and threads > 512:
@@ -71,6 +71,25 @@ def test_every_cfg(orc, keybits, direction):
         got, ok = gpu_ecb(direction, key, data, cfg=cfg, guard=64)
         assert ok, repr(cfg)
         assert np.array_equal(got, exp), repr(cfg)
+    assert aesgb.aes_wait_timeouts() == 0
+
+
+@pytest.mark.parametrize("keybits", KEYBITS)
+@pytest.mark.parametrize("direction", [0, 1])
+def test_tma_staged_edge_sizes(orc, keybits, direction):
+    """The TMA-staged kernel at sizes around its tile (32 x blocks_per_thread
+    blocks per warp and pass): partial first tiles, warps without work, and a
+    partial last tile, in place and out of place; no bounded wait runs out."""
+    key = wl.random_key(keybits, 11).tobytes()
+    for cfg in (aesgb.make_cfg(1024, 2, aesgb.LAYOUT_R4_TMA, 1), aesgb.make_cfg(64, 4, aesgb.LAYOUT_R4_TMA, 0)):
+        for n in (1, 2, 31, 32, 33, 63, 64, 65, 127, 129, 1023, 1025, 4097, 65_537):
+            data = wl.random_bytes(16 * n, 100 + n)
+            exp = oracle_ecb(orc, direction, key, data)
+            got, ok = gpu_ecb(direction, key, data, cfg=cfg, guard=64)
+            assert ok and np.array_equal(got, exp), (repr(cfg), n)
+            got, ok = gpu_ecb(direction, key, data, cfg=cfg, inplace=True, guard=64)
+            assert ok and np.array_equal(got, exp), (repr(cfg), n, "in place")
+    assert aesgb.aes_wait_timeouts() == 0
 
 
 @pytest.mark.parametrize("keybits", KEYBITS)
