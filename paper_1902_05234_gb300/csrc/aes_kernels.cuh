@@ -242,6 +242,16 @@ __device__ __forceinline__ void cipher_states(const TabT &tab, const Key &k, uin
     for (int i = 0; i < NB; ++i) final_round<DIR>(tab, s[i], k, 4 * NR);
 }
 
+// Programmatic dependent launch.  The host launches the single-buffer kernels
+// with programmatic stream serialisation (launch_pdl), so a kernel may start
+// -- fill its tables, which reads only constant memory -- while the previous
+// kernel in the stream is still draining.  griddep_wait() returns once that
+// kernel has completed and its writes are visible; every global load or store
+// comes after it.  griddep_release() lets the next such kernel start early.
+// Both are no-ops in a launch without the attribute.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ uint4 ld_block(const uint4 *p) { return __ldcs(p); }
 __device__ __forceinline__ void st_block(uint4 *p, uint4 v) { __stcs(p, v); }
 
@@ -261,16 +271,17 @@ __global__ void __launch_bounds__(max_threads_for_nb(NB), 1)
     const unsigned long long step = static_cast<unsigned long long>(gridDim.x) * wpc * 32ull * NB;
     unsigned long long base = (blockIdx.x * wpc + (threadIdx.x >> 5)) * 32ull * NB;
 
-    // The first pass's loads are issued before the table fill, so their HBM
-    // latency overlaps it (this is most of a small launch's fixed cost).
+    Tab<LAYOUT, DIR>::fill(smem, threadIdx.x, blockDim.x);
+    __syncthreads();
+    griddep_release();
+    griddep_wait();
+
     uint4 cur[NB];
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
         const unsigned long long b = base + lane + 32ull * i;
         cur[i] = b < n ? ld_block(a.in + b) : make_uint4(0, 0, 0, 0);
     }
-    Tab<LAYOUT, DIR>::fill(smem, threadIdx.x, blockDim.x);
-    __syncthreads();
 
     const Tab<LAYOUT, DIR> tab(smem, lane);
     const ParamKey key{a.rk.w};

@@ -130,6 +130,24 @@ int persistent_grid(const void *fn, int dev, const aes_launch_cfg &c, uint32_t s
     return AES_OK;
 }
 
+int launch_pdl(const void *fn, int grid, int threads, uint32_t smem, void **params, void *stream) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(grid));
+    cfg.blockDim = dim3(static_cast<unsigned>(threads));
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = static_cast<cudaStream_t>(stream);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelExC(&cfg, fn, params) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return AES_E_CUDA;
+    }
+    return AES_OK;
+}
+
 int launch_ecb(int dir, const uint32_t *rk, int nr, const uint8_t *in, uint8_t *out, size_t nblocks,
                const aes_launch_cfg &c, void *stream) {
     const void *fn = ecb_kernel_ptr(dir, nr, c.blocks_per_thread, c.layout);
@@ -149,13 +167,7 @@ int launch_ecb(int dir, const uint32_t *rk, int nr, const uint8_t *in, uint8_t *
     args.nblocks = nblocks;
     order_round_keys(dir, rk, nr, &args.rk);
     void *params[] = {&args};
-    const cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(c.threads), params, smem,
-                                           static_cast<cudaStream_t>(stream));
-    if (e != cudaSuccess) {
-        (void)cudaGetLastError();
-        return AES_E_CUDA;
-    }
-    return AES_OK;
+    return launch_pdl(fn, grid, c.threads, smem, params, stream);
 }
 
 }  // namespace aesgb

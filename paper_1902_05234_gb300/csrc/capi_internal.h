@@ -12,6 +12,10 @@ struct RoundKeys;
 int current_device(int *dev);
 int sm_count(int dev);
 int ensure_smem_attr(const void *fn, int dev, uint32_t bytes);
+// Launch `fn` with programmatic stream serialisation (the kernel may start
+// before the previous kernel in the stream completes; it must call
+// griddep_wait() before touching global memory).  AES_E_CUDA on failure.
+int launch_pdl(const void *fn, int grid, int threads, uint32_t smem, void **params, void *stream);
 int check_nrounds(int nr);
 int check_buffers(const void *in, const void *out, size_t nblocks);
 void order_round_keys(int dir, const uint32_t *rk, int nr, RoundKeys *out);

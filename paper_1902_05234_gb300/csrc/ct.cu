@@ -87,6 +87,8 @@ __global__ void __launch_bounds__(kCtThreads, 1) ct_kernel(const __grid_constant
     __shared__ bs::RoundMasks masks[15];
     for (int i = threadIdx.x; i < (a.nr + 1) * 128; i += blockDim.x) expand_mask(a.masks, i, masks);
     __syncthreads();
+    griddep_release();
+    griddep_wait();  // global memory only after this (see aes_kernels.cuh)
     const uint32_t lane = threadIdx.x & 31u;
     const unsigned long long wpc = blockDim.x >> 5;
     const unsigned long long step = static_cast<unsigned long long>(gridDim.x) * wpc * 1024ull;
@@ -146,12 +148,7 @@ int aes_ecb_crypt_ct(int dir, const uint32_t *rk, int nrounds, const uint8_t *in
     st = persistent_grid(fn, dev, c, 0, static_cast<unsigned long long>(kCtThreads) * 32ull, nblocks, &grid);
     if (st != AES_OK) return st;
     void *params[] = {&args};
-    if (cudaLaunchKernel(fn, dim3(grid), dim3(kCtThreads), params, 0, static_cast<cudaStream_t>(stream)) !=
-        cudaSuccess) {
-        (void)cudaGetLastError();
-        return AES_E_CUDA;
-    }
-    return AES_OK;
+    return launch_pdl(fn, grid, kCtThreads, 0, params, stream);
 }
 
 int aes_ct_ops_per_block(int dir, int nrounds, double *ops_per_block) {

@@ -93,12 +93,16 @@ __global__ void __launch_bounds__(max_threads_for_nb(NB), 1) ecb_tma_kernel(cons
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    Tab<kLayoutR4, DIR>::fill(smem, threadIdx.x, blockDim.x);
+    __syncthreads();
+    griddep_release();
+    griddep_wait();  // global memory (the bulk copies included) only after this
+    if (lane == 0) {
         issue(base, 0);
         issue(base + step, 1);
     }
     __syncwarp();
-    Tab<kLayoutR4, DIR>::fill(smem, threadIdx.x, blockDim.x);
-    __syncthreads();
 
     const Tab<kLayoutR4, DIR> tab(smem, lane);
     const ParamKey key{a.rk.w};

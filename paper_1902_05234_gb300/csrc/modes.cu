@@ -60,14 +60,16 @@ __global__ void __launch_bounds__(max_threads_for_nb(NB), 1) ctr_kernel(const __
     const unsigned long long wpc = blockDim.x >> 5;
     const unsigned long long step = static_cast<unsigned long long>(gridDim.x) * wpc * 32ull * NB;
     unsigned long long base = (blockIdx.x * wpc + (threadIdx.x >> 5)) * 32ull * NB;
-    uint4 cur[NB];  // first pass loaded before the table fill, as in ecb_kernel
+    Tab<LAYOUT, kEncrypt>::fill(smem, threadIdx.x, blockDim.x);
+    __syncthreads();
+    griddep_release();
+    griddep_wait();  // global memory only after this (see aes_kernels.cuh)
+    uint4 cur[NB];
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
         const unsigned long long b = base + lane + 32ull * i;
         cur[i] = b < n ? ld_block(a.in + b) : make_uint4(0, 0, 0, 0);
     }
-    Tab<LAYOUT, kEncrypt>::fill(smem, threadIdx.x, blockDim.x);
-    __syncthreads();
     const Tab<LAYOUT, kEncrypt> tab(smem, lane);
     const ParamKey key{a.rk.w};
     for (; base < n; base += step) {
@@ -109,14 +111,16 @@ __global__ void __launch_bounds__(max_threads_for_nb(NB), 1) cbc_dec_kernel(cons
     const unsigned long long wpc = blockDim.x >> 5;
     const unsigned long long step = static_cast<unsigned long long>(gridDim.x) * wpc * 32ull * NB;
     unsigned long long base = (blockIdx.x * wpc + (threadIdx.x >> 5)) * 32ull * NB;
-    uint4 cur[NB];  // first pass loaded before the table fill, as in ecb_kernel
+    Tab<LAYOUT, kDecrypt>::fill(smem, threadIdx.x, blockDim.x);
+    __syncthreads();
+    griddep_release();
+    griddep_wait();  // global memory only after this (see aes_kernels.cuh)
+    uint4 cur[NB];
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
         const unsigned long long b = base + lane + 32ull * i;
         cur[i] = b < n ? ld_block(a.in + b) : make_uint4(0, 0, 0, 0);
     }
-    Tab<LAYOUT, kDecrypt>::fill(smem, threadIdx.x, blockDim.x);
-    __syncthreads();
     const Tab<LAYOUT, kDecrypt> tab(smem, lane);
     const ParamKey key{a.rk.w};
     for (; base < n; base += step) {
@@ -189,12 +193,7 @@ int launch_mode(const void *fn, int dir, const aes_launch_cfg &c, size_t nblocks
                          nblocks, &grid);
     if (st != AES_OK) return st;
     void *params[] = {&args};
-    if (cudaLaunchKernel(fn, dim3(grid), dim3(c.threads), params, smem, static_cast<cudaStream_t>(stream)) !=
-        cudaSuccess) {
-        (void)cudaGetLastError();
-        return AES_E_CUDA;
-    }
-    return AES_OK;
+    return launch_pdl(fn, grid, c.threads, smem, params, stream);
 }
 
 }  // namespace

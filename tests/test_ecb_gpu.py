@@ -193,3 +193,40 @@ def test_lookup_rate_calibration():
     assert 1e9 < rate < 32 * 3.0e9           # below 32 per clock at any plausible clock
     with pytest.raises(aesgb.AesError):
         aesgb.aes_calibrate_lookup_rate(sink, 16)
+
+
+@pytest.mark.parametrize("keybits", [128, 256])
+def test_back_to_back_dependent_launches(orc, keybits):
+    """Kernels launched back to back on one stream, each reading what the one
+    before wrote.  The single-buffer kernels are launched with programmatic
+    stream serialisation (they may start while the previous kernel drains and
+    wait for it before touching global memory), so a missing wait would show
+    here: 12 in-place encryptions through the register-path, R1, TMA-staged
+    and constant-time kernels in turn, then 12 decryptions, no synchronisation
+    in between, against the oracle applied as many times."""
+    torch = torch_cuda()
+    key = wl.random_key(keybits, 21).tobytes()
+    enc, dec, nr = aesgb.aes_expand_key(keybits, key)
+    cfgs = [None, aesgb.make_cfg(1024, 2, aesgb.LAYOUT_R1, 0), aesgb.make_cfg(1024, 2, aesgb.LAYOUT_R4_TMA, 0), "ct"]
+    k = 12
+    for n in (1, 33, 4097, 300_001):
+        data = wl.random_bytes(16 * n, 200 + n)
+        x = torch.from_numpy(data.copy()).cuda()
+        for direction, rk in ((0, enc), (1, dec)):
+            for i in range(k):
+                cfg = cfgs[i % len(cfgs)]
+                if cfg is None:
+                    (aesgb.aes_ecb_encrypt if direction == 0 else aesgb.aes_ecb_decrypt)(rk, nr, x, x, n)
+                elif cfg == "ct":
+                    aesgb.aes_ecb_crypt_ct(direction, rk, nr, x, x, n)
+                else:
+                    aesgb.aes_ecb_crypt_cfg(direction, rk, nr, x, x, n, cfg)
+            if direction == 0:
+                torch.cuda.synchronize()
+                exp = data
+                for _ in range(k):
+                    exp = orc.ecb(0, key, exp, nthreads=16)
+                assert np.array_equal(x.cpu().numpy(), exp), n
+        torch.cuda.synchronize()
+        assert np.array_equal(x.cpu().numpy(), data), n
+    assert aesgb.aes_wait_timeouts() == 0
