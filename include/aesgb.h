@@ -78,6 +78,16 @@ int aes_version(void);
  * from the counter). */
 int aes_wait_timeouts(unsigned long long *count);
 
+/* Failure-detection test hook: one warp of the TMA-staged encryption kernel
+ * on nblocks (1..64) DEVICE blocks, with every mbarrier expecting 16 bytes
+ * more than its bulk copy delivers.  The copies land, but no wait can finish:
+ * each runs out after about one second, the warp counts one timeout (read
+ * with aes_wait_timeouts), waits (bounded) for its copies and stops without
+ * writing `out`.  The context stays usable.  Async on `stream`; the kernel
+ * takes about 1-3 s.  AES_E_RANGE outside 1..64 blocks, AES_E_ALIGN /
+ * AES_E_OVERLAP as aes_ecb_encrypt. */
+int aes_tma_selftest_timeout(const uint8_t *in, uint8_t *out, size_t nblocks, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Key schedule (host)                                                       */
 /* ------------------------------------------------------------------------ */

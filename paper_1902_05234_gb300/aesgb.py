@@ -111,6 +111,7 @@ _SIGNATURES = {
     "aes_ct_selftest_host": (_i, [_i, _u32p, _i, _vp, _vp, _sz]),
     "aes_ct_ops_per_block": (_i, [_i, _i, ctypes.POINTER(ctypes.c_double)]),
     "aes_wait_timeouts": (_i, [ctypes.POINTER(ctypes.c_ulonglong)]),
+    "aes_tma_selftest_timeout": (_i, [_vp, _vp, _sz, _vp]),
     "aes_ctr_crypt": (_i, [_u32p, _i, _u8p, _vp, _vp, _sz, _vp]),
     "aes_cbc_decrypt": (_i, [_u32p, _i, _u8p, _vp, _vp, _sz, _vp]),
     "aes_tune_ecb": (_i, [_i, _i, _u32p, _vp, _vp, _sz, _vp, ctypes.POINTER(aes_launch_cfg)]),
@@ -416,6 +417,12 @@ def aes_wait_timeouts() -> int:
     v = ctypes.c_ulonglong()
     _check(lib().aes_wait_timeouts(ctypes.byref(v)), "aes_wait_timeouts")
     return v.value
+
+
+def aes_tma_selftest_timeout(in_, out, nblocks: int, stream=None) -> None:
+    """Failure-detection test hook: a TMA-staged launch whose waits must run out."""
+    _check(lib().aes_tma_selftest_timeout(_ptr(in_), _ptr(out), int(nblocks), _stream(stream)),
+           "aes_tma_selftest_timeout")
 
 
 def aes_ct_ops_per_block(direction: int, nrounds: int) -> float:

@@ -166,7 +166,8 @@ int launch_ecb(int dir, const uint32_t *rk, int nr, const uint8_t *in, uint8_t *
     args.out = reinterpret_cast<uint4 *>(out);
     args.nblocks = nblocks;
     order_round_keys(dir, rk, nr, &args.rk);
-    void *params[] = {&args};
+    uint32_t extra_tx = 0;  // the TMA-staged kernel's second parameter
+    void *params[] = {&args, &extra_tx};
     return launch_pdl(fn, grid, c.threads, smem, params, stream);
 }
 
@@ -203,6 +204,13 @@ int aes_version(void) { return 10000; }
 int aes_wait_timeouts(unsigned long long *count) {
     if (!count) return AES_E_ARG;
     return read_wait_timeouts(count);
+}
+
+int aes_tma_selftest_timeout(const uint8_t *in, uint8_t *out, size_t nblocks, void *stream) {
+    if (nblocks == 0 || nblocks > 64) return AES_E_RANGE;
+    const int st = check_buffers(in, out, nblocks);
+    if (st != AES_OK) return st;
+    return launch_tma_selftest_timeout(in, out, nblocks, stream);
 }
 
 int aes_expand_key(int keybits, const uint8_t *key, uint32_t *rk_enc, uint32_t *rk_dec) {

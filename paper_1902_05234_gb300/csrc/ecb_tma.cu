@@ -68,8 +68,12 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
                  : "memory");
 }
 
+// extra_tx is 0 except in the failure-detection self-test
+// (aes_tma_selftest_timeout), where every barrier expects that many bytes more
+// than its copy delivers, so that no wait can finish and each must run out.
 template <int DIR, int NR, int NB>
-__global__ void __launch_bounds__(max_threads_for_nb(NB), 1) ecb_tma_kernel(const __grid_constant__ EcbArgs a) {
+__global__ void __launch_bounds__(max_threads_for_nb(NB), 1)
+    ecb_tma_kernel(const __grid_constant__ EcbArgs a, const uint32_t extra_tx) {
     extern __shared__ __align__(128) uint8_t smem[];
     constexpr uint32_t kTile = 512u * NB;  // one warp's blocks of one pass
     constexpr unsigned long long kTileBlocks = 32ull * NB;
@@ -86,7 +90,7 @@ __global__ void __launch_bounds__(max_threads_for_nb(NB), 1) ecb_tma_kernel(cons
         if (b >= n) return;
         const unsigned long long cnt = n - b < kTileBlocks ? n - b : kTileBlocks;
         const uint32_t bytes = static_cast<uint32_t>(cnt * 16ull);
-        mbar_arrive_expect_tx(&bar[buf], bytes);
+        mbar_arrive_expect_tx(&bar[buf], bytes + extra_tx);
         bulk_load(stage + buf * kTile, a.in + b, bytes, &bar[buf]);
     };
     if (lane == 0) {
@@ -161,6 +165,26 @@ const void *ecb_kernel_tma(int dir, int nr, int nb) {
 uint32_t ecb_tma_smem_bytes(int dir, int threads, int nb) {
     const uint32_t warps = static_cast<uint32_t>(threads / 32);
     return table_smem_bytes(dir, kLayoutR4) + warps * 2u * 512u * static_cast<uint32_t>(nb) + warps * 16u;
+}
+
+int launch_tma_selftest_timeout(const uint8_t *in, uint8_t *out, size_t nblocks, void *stream) {
+    const void *fn = reinterpret_cast<const void *>(&ecb_tma_kernel<kEncrypt, 10, 1>);
+    int dev = 0;
+    if (current_device(&dev) != AES_OK) return AES_E_CUDA;
+    const uint32_t smem = ecb_tma_smem_bytes(kEncrypt, 32, 1);
+    int st = ensure_smem_attr(fn, dev, smem);
+    if (st != AES_OK) return st;
+    EcbArgs args{};
+    args.in = reinterpret_cast<const uint4 *>(in);
+    args.out = reinterpret_cast<uint4 *>(out);
+    args.nblocks = nblocks;
+    uint32_t extra = 16;
+    void *params[] = {&args, &extra};
+    if (cudaLaunchKernel(fn, dim3(1), dim3(32), params, smem, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return AES_E_CUDA;
+    }
+    return AES_OK;
 }
 
 int read_wait_timeouts(unsigned long long *count) {

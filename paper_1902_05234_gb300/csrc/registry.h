@@ -16,6 +16,9 @@ const void *ecb_kernel_dec(int nr, int nb, int layout);
 const void *ecb_kernel_tma(int dir, int nr, int nb);
 uint32_t ecb_tma_smem_bytes(int dir, int threads, int nb);
 int read_wait_timeouts(unsigned long long *count);
+// One warp of the TMA-staged kernel whose barriers can never complete (see
+// aes_tma_selftest_timeout in aesgb.h).
+int launch_tma_selftest_timeout(const uint8_t *in, uint8_t *out, size_t nblocks, void *stream);
 
 // Copy table `which` (0 te0, 1 td0, 2 S-box, 3 InvS) from the constant bank of
 // the encrypt module on the current device.  Returns a cudaError_t value.

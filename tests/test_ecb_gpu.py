@@ -230,3 +230,26 @@ def test_back_to_back_dependent_launches(orc, keybits):
         torch.cuda.synchronize()
         assert np.array_equal(x.cpu().numpy(), data), n
     assert aesgb.aes_wait_timeouts() == 0
+
+
+def test_tma_wait_timeout_is_reported_and_context_survives(orc):
+    """Failure detection on the device without a fault: the TMA-staged kernel
+    run with barriers that can never complete (aes_tma_selftest_timeout).  Its
+    bounded waits run out, the warp reports one timeout and stops without
+    writing its output, and the context then runs ordinary launches."""
+    torch = torch_cuda()
+    n = 64
+    data = wl.random_bytes(16 * n, 31)
+    x = torch.from_numpy(data.copy()).cuda()
+    y = torch.full_like(x, 0x5A)
+    aesgb.aes_wait_timeouts()  # reset
+    aesgb.aes_tma_selftest_timeout(x, y, n)
+    torch.cuda.synchronize()
+    assert aesgb.aes_wait_timeouts() == 1
+    assert bool((y == 0x5A).all())
+    key = wl.random_key(128, 31).tobytes()
+    got, ok = gpu_ecb(0, key, data, cfg=aesgb.make_cfg(1024, 2, aesgb.LAYOUT_R4_TMA, 0), guard=64)
+    assert ok and np.array_equal(got, orc.ecb(0, key, data))
+    assert aesgb.aes_wait_timeouts() == 0
+    with pytest.raises(aesgb.AesError):
+        aesgb.aes_tma_selftest_timeout(x, y, 65)
