@@ -18,6 +18,9 @@
 //     completion times are recorded and their bytes leave the budget.
 // Host waits are bounded (condition variables with timeouts); nothing on the
 // device waits.  Latency is host arrival -> host-observed completion.
+#if defined(__linux__)
+#include <sys/prctl.h>
+#endif
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -57,11 +60,12 @@ struct Req {
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
+    // One page-locked buffer and its device copy per slot, uploaded with one
+    // copy per batch: n descriptors at the start, the host-built plan (the
+    // batch kernel's workspace) at the next 256-byte boundary.
     aes_desc *h_desc = nullptr;
     aes_desc *d_desc = nullptr;
-    void *h_ws = nullptr;  // page-locked: the batch plan built on the host
-    void *d_ws = nullptr;
-    size_t ws_bytes = 0;
+    size_t buf_bytes = 0;
     bool busy = false;
     size_t bytes = 0;
     std::vector<uint64_t> tickets;
@@ -98,14 +102,16 @@ void free_server(Server *s) {
         if (sl.ev) cudaEventDestroy(sl.ev);
         if (sl.stream) cudaStreamDestroy(sl.stream);
         if (sl.h_desc) cudaFreeHost(sl.h_desc);
-        if (sl.h_ws) cudaFreeHost(sl.h_ws);
         if (sl.d_desc) cudaFree(sl.d_desc);
-        if (sl.d_ws) cudaFree(sl.d_ws);
     }
     if (s->d_rk_enc) cudaFree(s->d_rk_enc);
     if (s->d_rk_dec) cudaFree(s->d_rk_dec);
     delete s;
 }
+
+// Offset of the plan in a slot's buffer, after n descriptors (the workspace
+// wants 256-byte alignment).
+size_t plan_offset(int n) { return (sizeof(aes_desc) * static_cast<size_t>(n) + 255) & ~static_cast<size_t>(255); }
 
 // Batch configuration for a batch of `total_blocks`: chunks small enough that
 // every warp of the grid gets several (latency at light load), at most the
@@ -190,12 +196,12 @@ bool dispatch_locked(Server *s, int sms) {
     // the host -- every request was validated at submission -- and uploaded
     // with the descriptors, so only the persistent kernel runs on the device
     const aes_batch_cfg cfg = serve_cfg(sms, blocks);
-    plan_on_host(sl->h_desc, n, batch_chunk_blocks(cfg), sl->h_ws);
-    bool ok = cudaMemcpyAsync(sl->d_desc, sl->h_desc, sizeof(aes_desc) * n, cudaMemcpyHostToDevice,
+    const size_t ws_off = plan_offset(n);
+    plan_on_host(sl->h_desc, n, batch_chunk_blocks(cfg), reinterpret_cast<uint8_t *>(sl->h_desc) + ws_off);
+    bool ok = cudaMemcpyAsync(sl->d_desc, sl->h_desc, ws_off + batch_ws_bytes(n), cudaMemcpyHostToDevice,
                               sl->stream) == cudaSuccess;
-    ok = ok && cudaMemcpyAsync(sl->d_ws, sl->h_ws, batch_ws_bytes(n), cudaMemcpyHostToDevice, sl->stream) ==
-                   cudaSuccess;
-    ok = ok && enqueue_batch_kernel(sl->d_desc, n, sl->d_ws, cfg, sl->stream) == AES_OK;
+    ok = ok && enqueue_batch_kernel(sl->d_desc, n, reinterpret_cast<uint8_t *>(sl->d_desc) + ws_off, cfg,
+                                    sl->stream) == AES_OK;
     ok = ok && cudaEventRecord(sl->ev, sl->stream) == cudaSuccess;
     if (!ok) {
         (void)cudaGetLastError();
@@ -221,6 +227,13 @@ bool dispatch_locked(Server *s, int sms) {
 
 void worker_main(Server *s) {
     cudaSetDevice(s->dev);
+#if defined(__linux__)
+    // The dispatcher's timed waits are microseconds (event polls, arrival
+    // times); a normal thread's default 50 us timer slack would stretch each
+    // one to tens of microseconds, which is most of a light-load request's
+    // latency.  This thread's slack only, for its lifetime.
+    (void)prctl(PR_SET_TIMERSLACK, 1UL, 0UL, 0UL, 0UL);
+#endif
     const int sms = sm_count(s->dev) > 0 ? sm_count(s->dev) : 1;
     std::unique_lock<std::mutex> lk(s->mu);
     while (!s->stop) {
@@ -233,8 +246,9 @@ void worker_main(Server *s) {
         for (const Slot &sl : s->slots) any_busy |= sl.busy;
         if (launched) continue;
         if (any_busy) {
-            // poll the slots' events again shortly (host side, bounded)
-            s->cv_work.wait_for(lk, std::chrono::microseconds(10));
+            // poll the slots' events again shortly (host side, bounded); a
+            // completion is seen within a few microseconds
+            s->cv_work.wait_for(lk, std::chrono::microseconds(3));
         } else if (!s->pending.empty()) {
             const double wait = s->find(s->pending.front())->arrival - now_s();
             if (wait > 0)
@@ -272,13 +286,13 @@ int aes_srv_create(size_t mem_budget_bytes, int max_keys, int max_batch, int slo
     s->slots.resize(static_cast<size_t>(slots));
     for (Slot &sl : s->slots) {
         if (!ok) break;
-        sl.ws_bytes = aes_batch_workspace_bytes(max_batch);
+        sl.buf_bytes = plan_offset(max_batch) + aes_batch_workspace_bytes(max_batch);
+        void *hb = nullptr, *db = nullptr;
         ok = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) == cudaSuccess &&
              cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) == cudaSuccess &&
-             cudaMallocHost(&sl.h_desc, sizeof(aes_desc) * max_batch) == cudaSuccess &&
-             cudaMallocHost(&sl.h_ws, sl.ws_bytes) == cudaSuccess &&
-             cudaMalloc(&sl.d_desc, sizeof(aes_desc) * max_batch) == cudaSuccess &&
-             cudaMalloc(&sl.d_ws, sl.ws_bytes) == cudaSuccess;
+             cudaMallocHost(&hb, sl.buf_bytes) == cudaSuccess && cudaMalloc(&db, sl.buf_bytes) == cudaSuccess;
+        sl.h_desc = static_cast<aes_desc *>(hb);
+        sl.d_desc = static_cast<aes_desc *>(db);
         sl.tickets.reserve(static_cast<size_t>(max_batch));
     }
     if (!ok) {
