@@ -115,12 +115,18 @@ __global__ void __launch_bounds__(max_threads_for_nb(NB), 1) cbc_dec_kernel(cons
     __syncthreads();
     griddep_release();
     griddep_wait();  // global memory only after this (see aes_kernels.cuh)
+    // the ciphertext block just before a slice (lane 0's chaining value; the
+    // IV before block 0), loaded one pass ahead like the slice itself
+    auto before = [&](unsigned long long b) {
+        return b == 0 ? a.iv : (lane == 0 && b < n ? ld_block(a.in + (b - 1)) : make_uint4(0, 0, 0, 0));
+    };
     uint4 cur[NB];
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
         const unsigned long long b = base + lane + 32ull * i;
         cur[i] = b < n ? ld_block(a.in + b) : make_uint4(0, 0, 0, 0);
     }
+    uint4 before_cur = before(base);
     const Tab<LAYOUT, kDecrypt> tab(smem, lane);
     const ParamKey key{a.rk.w};
     for (; base < n; base += step) {
@@ -130,9 +136,10 @@ __global__ void __launch_bounds__(max_threads_for_nb(NB), 1) cbc_dec_kernel(cons
             const unsigned long long b = base + step + lane + 32ull * i;
             nxt[i] = b < n ? ld_block(a.in + b) : make_uint4(0, 0, 0, 0);
         }
+        const uint4 before_nxt = before(base + step);
         // chaining values: the ciphertext block just before each of ours
         uint4 prev[NB];
-        const uint4 before_slice0 = base == 0 ? a.iv : ld_block(a.in + (base - 1));
+        const uint4 before_slice0 = before_cur;
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
             const uint4 up = shfl_up1(cur[i]);
@@ -153,6 +160,7 @@ __global__ void __launch_bounds__(max_threads_for_nb(NB), 1) cbc_dec_kernel(cons
                                                prev[i].w ^ s[i][3]));
             cur[i] = nxt[i];
         }
+        before_cur = before_nxt;
     }
 }
 
