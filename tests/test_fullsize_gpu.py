@@ -17,6 +17,9 @@ checked against the oracle, properties over the whole buffer on the device.
 * 1 GiB, AES-128 (the benchmark's workload): every tuner candidate gives the
   same ciphertext (checked against the oracle on windows) and decrypts it back;
   every batch-tuner candidate gives the same 5.2 GB batch output.
+* 1 GiB through the other kernels the benchmark times: the constant-time
+  kernel (every key size), the TMA-staged layout, CTR and CBC decryption --
+  oracle windows, and round trips over the whole buffer.
 """
 import numpy as np
 import pytest
@@ -232,3 +235,87 @@ def test_batch_every_tuner_candidate_fullsize():
                 aesgb.aes_ecb_batch_ws(desc, n, ws, ws_bytes, cfg=aesgb.make_batch_cfg(th, nb, passes, 1))
                 torch.cuda.synchronize()
                 assert torch.equal(dst, ref), (nb, th, passes)
+
+
+def _windows(nbytes, win, seed):
+    g = wl.rng(seed)
+    return [0, nbytes - win] + [int(v) // 16 * 16 for v in g.integers(0, nbytes - win, 3)]
+
+
+@pytest.mark.parametrize("keybits", [128, 192, 256])
+def test_1gib_constant_time_windows_and_roundtrip(orc, keybits):
+    """The bitsliced kernel at the size the benchmark times it (1 GiB, every
+    key size): windows against the oracle, decryption in place back to the
+    plaintext over the whole buffer."""
+    torch = torch_cuda()
+    nbytes = GIB
+    n = nbytes // 16
+    x = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    _fill_random(torch, x, 70 + keybits)
+    key = wl.random_key(keybits, 70).tobytes()
+    enc, dec, nr = aesgb.aes_expand_key(keybits, key)
+    y = torch.empty_like(x)
+    aesgb.aes_ecb_crypt_ct(0, enc, nr, x, y, n)
+    torch.cuda.synchronize()
+    win = 64 * 1024
+    for s in _windows(nbytes, win, 71):
+        assert np.array_equal(y[s:s + win].cpu().numpy(), orc.ecb(0, key, x[s:s + win].cpu().numpy(), nthreads=16)), s
+    aesgb.aes_ecb_crypt_ct(1, dec, nr, y, y, n)
+    torch.cuda.synchronize()
+    assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("cfg", [(1024, 2), (512, 4)])
+def test_1gib_tma_staged_windows_and_roundtrip(orc, cfg):
+    """The TMA-staged layout at 1 GiB (the study's configurations): windows
+    against the oracle, in-place decryption back, no bounded wait run out."""
+    torch = torch_cuda()
+    nbytes = GIB
+    n = nbytes // 16
+    x = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    _fill_random(torch, x, 72)
+    key = wl.random_key(128, 72).tobytes()
+    enc, dec, nr = aesgb.aes_expand_key(128, key)
+    c = aesgb.make_cfg(cfg[0], cfg[1], aesgb.LAYOUT_R4_TMA, 0)
+    y = torch.empty_like(x)
+    aesgb.aes_ecb_crypt_cfg(0, enc, nr, x, y, n, c)
+    torch.cuda.synchronize()
+    win = 64 * 1024
+    for s in _windows(nbytes, win, 73):
+        assert np.array_equal(y[s:s + win].cpu().numpy(), orc.ecb(0, key, x[s:s + win].cpu().numpy(), nthreads=16)), s
+    aesgb.aes_ecb_crypt_cfg(1, dec, nr, y, y, n, c)
+    torch.cuda.synchronize()
+    assert torch.equal(x, y)
+    assert aesgb.aes_wait_timeouts() == 0
+
+
+@pytest.mark.parametrize("keybits", [128, 256])
+def test_1gib_ctr_and_cbc_decrypt_windows(orc, keybits):
+    """CTR and CBC decryption at the size the benchmark times them (1 GiB):
+    windows against the oracle, each started from its own counter block or
+    chaining block; CTR applied twice gives the input back."""
+    torch = torch_cuda()
+    nbytes = GIB
+    n = nbytes // 16
+    x = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    _fill_random(torch, x, 74 + keybits)
+    key = wl.random_key(keybits, 74).tobytes()
+    enc, dec, nr = aesgb.aes_expand_key(keybits, key)
+    ctr0 = np.frombuffer(bytes(range(240, 256)), np.uint8)  # low bytes near a carry
+    iv = np.frombuffer(bytes(range(16)), np.uint8)
+    y = torch.empty_like(x)
+    win = 64 * 1024
+    aesgb.aes_ctr_crypt(enc, nr, ctr0, x, y, n)
+    torch.cuda.synchronize()
+    for s in _windows(nbytes, win, 75):
+        exp = orc.ctr(key, orc.ctr_block(ctr0, s // 16), x[s:s + win].cpu().numpy())
+        assert np.array_equal(y[s:s + win].cpu().numpy(), exp), ("ctr", s)
+    aesgb.aes_ctr_crypt(enc, nr, ctr0, y, y, n)
+    torch.cuda.synchronize()
+    assert torch.equal(x, y)
+    aesgb.aes_cbc_decrypt(dec, nr, iv, x, y, n)
+    torch.cuda.synchronize()
+    for s in _windows(nbytes, win, 76):
+        chain = iv if s == 0 else x[s - 16:s].cpu().numpy()
+        exp = orc.cbc_decrypt(key, chain, x[s:s + win].cpu().numpy())
+        assert np.array_equal(y[s:s + win].cpu().numpy(), exp), ("cbc", s)
