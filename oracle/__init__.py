@@ -54,6 +54,8 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
         "orc_ctr": (None, [_u8p, ctypes.c_int, _u8p, _u8p, _u8p, ctypes.c_size_t]),
         "orc_cbc_encrypt": (None, [_u8p, ctypes.c_int, _u8p, _u8p, _u8p, ctypes.c_size_t]),
         "orc_cbc_decrypt": (None, [_u8p, ctypes.c_int, _u8p, _u8p, _u8p, ctypes.c_size_t]),
+        "orc_cfb_encrypt": (None, [_u8p, ctypes.c_int, _u8p, _u8p, _u8p, ctypes.c_size_t]),
+        "orc_cfb_decrypt": (None, [_u8p, ctypes.c_int, _u8p, _u8p, _u8p, ctypes.c_size_t]),
         "orc_mutant_id": (ctypes.c_int, []),
     }
     for name, (res, args) in sig.items():
@@ -215,4 +217,18 @@ class Oracle:
         src, v = _bytes(data), _bytes(iv)
         out = np.empty_like(src)
         self.lib.orc_cbc_decrypt(_p(w), nr, _p(v), _p(src), _p(out), src.size // 16)
+        return out
+
+    def cfb_encrypt(self, key, iv, data) -> np.ndarray:
+        w, nr = self.key_expansion(key)
+        src, v = _bytes(data), _bytes(iv)
+        out = np.empty_like(src)
+        self.lib.orc_cfb_encrypt(_p(w), nr, _p(v), _p(src), _p(out), src.size // 16)
+        return out
+
+    def cfb_decrypt(self, key, iv, data) -> np.ndarray:
+        w, nr = self.key_expansion(key)
+        src, v = _bytes(data), _bytes(iv)
+        out = np.empty_like(src)
+        self.lib.orc_cfb_decrypt(_p(w), nr, _p(v), _p(src), _p(out), src.size // 16)
         return out

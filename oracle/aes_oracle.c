@@ -30,6 +30,8 @@
  *   orc_ctr           CTR, eq (5): C_i = P_i xor cipher(counter block of block i)
  *   orc_cbc_encrypt / orc_cbc_decrypt   CBC (eq (2) as intended: the printed
  *                     equation omits the cipher; NIST SP 800-38A reading)
+ *   orc_cfb_encrypt / orc_cfb_decrypt   CFB (eq (3) read by the text beside
+ *                     it: full-block CFB of NIST SP 800-38A)
  *
  * State layout (FIPS-197 3.4): s[r][c] = in[r + 4c], r = row, c = column.
  * Round key i is bytes w[16 i .. 16 i + 15] of the expanded key, column-major
@@ -456,6 +458,44 @@ void orc_cbc_decrypt(const uint8_t *w, int nr, const uint8_t iv[16], const uint8
         orc_inv_cipher(w, nr, c, x);
         for (int b = 0; b < 16; ++b) out[16 * i + b] = x[b] ^ prev[b];
         memcpy(prev, c, 16);
+    }
+}
+
+/* CFB.  eq (3) as printed feeds C_{i-1} xor P_{i-1} to the cipher, which
+ * contradicts the text beside it (the mode is fed with the ciphertext, not
+ * the plaintext, of the previous block); the reading is the text's, as in
+ * NIST SP 800-38A with full 16-byte segments: C_i = P_i xor cipher(C_{i-1}),
+ * C_0 = IV, and P_i = C_i xor cipher(C_{i-1}) -- the forward cipher in both
+ * directions.  MUTANT(14) follows the printed equation instead. */
+void orc_cfb_encrypt(const uint8_t *w, int nr, const uint8_t iv[16], const uint8_t *in,
+                     uint8_t *out, size_t nblocks) {
+    uint8_t prev_c[16], prev_p[16];
+    memcpy(prev_c, iv, 16);
+    memset(prev_p, 0, 16);
+    for (size_t i = 0; i < nblocks; ++i) {
+        uint8_t x[16], ks[16], p[16];
+        memcpy(p, in + 16 * i, 16); /* keep P_i: out may alias in */
+        for (int b = 0; b < 16; ++b) x[b] = (uint8_t)(prev_c[b] ^ (MUTANT(14) ? prev_p[b] : 0));
+        orc_cipher(w, nr, x, ks);
+        for (int b = 0; b < 16; ++b) out[16 * i + b] = p[b] ^ ks[b];
+        memcpy(prev_c, out + 16 * i, 16);
+        memcpy(prev_p, p, 16);
+    }
+}
+
+void orc_cfb_decrypt(const uint8_t *w, int nr, const uint8_t iv[16], const uint8_t *in,
+                     uint8_t *out, size_t nblocks) {
+    uint8_t prev_c[16], prev_p[16];
+    memcpy(prev_c, iv, 16);
+    memset(prev_p, 0, 16);
+    for (size_t i = 0; i < nblocks; ++i) {
+        uint8_t c[16], x[16], ks[16];
+        memcpy(c, in + 16 * i, 16); /* keep C_i: out may alias in */
+        for (int b = 0; b < 16; ++b) x[b] = (uint8_t)(prev_c[b] ^ (MUTANT(14) ? prev_p[b] : 0));
+        orc_cipher(w, nr, x, ks);
+        for (int b = 0; b < 16; ++b) out[16 * i + b] = c[b] ^ ks[b];
+        memcpy(prev_c, c, 16);
+        memcpy(prev_p, out + 16 * i, 16);
     }
 }
 

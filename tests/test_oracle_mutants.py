@@ -25,6 +25,7 @@ MUTANTS = {
     11: "equivalent-inverse schedule also transforms round key 0",
     12: "CTR counter incremented little-endian",
     13: "T1 built with the coefficients of T3",
+    14: "CFB feeds C_{i-1} xor P_{i-1} to the cipher (eq (3) as printed)",
 }
 
 
