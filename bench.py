@@ -760,15 +760,16 @@ def ct_roofline(aesgb, ct, nbytes, keybits, sms, f_mhz):
 
 
 def run_modes(torch, aesgb, src, nbytes, key, keybits, iters=5):
-    """CTR and parallel CBC decryption on the same buffer (same tables and
-    round code as ECB, so the same shared-memory lookup bound)."""
+    """CTR and parallel CBC / CFB decryption on the same buffer (same tables
+    and round code as ECB, so the same shared-memory lookup bound)."""
     n = nbytes // 16
     enc, dec, nr = aesgb.aes_expand_key(keybits, key)
     dst = torch.empty_like(src)
     out = {}
     iv = bytes(range(16))
     for name, fn in (("ctr", lambda: aesgb.aes_ctr_crypt(enc, nr, iv, src, dst, n)),
-                     ("cbc_decrypt", lambda: aesgb.aes_cbc_decrypt(dec, nr, iv, src, dst, n))):
+                     ("cbc_decrypt", lambda: aesgb.aes_cbc_decrypt(dec, nr, iv, src, dst, n)),
+                     ("cfb_decrypt", lambda: aesgb.aes_cfb_decrypt(enc, nr, iv, src, dst, n))):
         fn()
         s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s_.record()

@@ -301,6 +301,16 @@ int aes_ctr_crypt(const uint32_t *rk, int nrounds, const uint8_t *ctr0, const ui
 int aes_cbc_decrypt(const uint32_t *rk_dec, int nrounds, const uint8_t *iv, const uint8_t *in, uint8_t *out,
                     size_t nblocks, void *stream);
 
+/* CFB decryption (section 3.1.3, with eq (3) read as its text states --
+ * the mode is fed with the previous ciphertext -- i.e. full-block CFB of
+ * NIST SP 800-38A: C_i = P_i xor E(C_{i-1}), C_{-1} = iv): P_i = C_i xor
+ * E(C_{i-1}), the FORWARD cipher, so rk = rk_enc from aes_expand_key.  Every
+ * block needs only two ciphertext blocks, so it runs in parallel.  iv HOST,
+ * 16 bytes; in/out DEVICE, disjoint (in place is AES_E_OVERLAP, as for CBC).
+ * CFB encryption chains block to block and is not offered (Table 1). */
+int aes_cfb_decrypt(const uint32_t *rk_enc, int nrounds, const uint8_t *iv, const uint8_t *in, uint8_t *out,
+                    size_t nblocks, void *stream);
+
 /* Release every resource the library created lazily (internal streams and
  * events, batch workspaces, tuner state) on all devices.  Call with no work
  * of the library in flight. */

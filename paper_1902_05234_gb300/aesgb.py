@@ -114,6 +114,7 @@ _SIGNATURES = {
     "aes_tma_selftest_timeout": (_i, [_vp, _vp, _sz, _vp]),
     "aes_ctr_crypt": (_i, [_u32p, _i, _u8p, _vp, _vp, _sz, _vp]),
     "aes_cbc_decrypt": (_i, [_u32p, _i, _u8p, _vp, _vp, _sz, _vp]),
+    "aes_cfb_decrypt": (_i, [_u32p, _i, _u8p, _vp, _vp, _sz, _vp]),
     "aes_tune_ecb": (_i, [_i, _i, _u32p, _vp, _vp, _sz, _vp, ctypes.POINTER(aes_launch_cfg)]),
     "aes_tune_batch": (_i, [_vp, _i, _vp, _sz, _vp, ctypes.POINTER(aes_batch_cfg)]),
     "aes_tune_set_ecb": (_i, [_i, _i, _sz, ctypes.POINTER(aes_launch_cfg)]),
@@ -440,6 +441,13 @@ def aes_ct_selftest_host(direction: int, rk, nrounds: int, data: np.ndarray) -> 
     _check(lib().aes_ct_selftest_host(int(direction), p, int(nrounds), src.ctypes.data, out.ctypes.data,
                                       src.size // 16), "aes_ct_selftest_host")
     return out
+
+
+def aes_cfb_decrypt(rk_enc, nrounds: int, iv, in_, out, nblocks: int, stream=None) -> None:
+    p, _keep = _rk_arg(rk_enc)
+    v = _block16(iv)
+    _check(lib().aes_cfb_decrypt(p, int(nrounds), v.ctypes.data_as(_u8p), _ptr(in_), _ptr(out), int(nblocks),
+                                 _stream(stream)), "aes_cfb_decrypt")
 
 
 def _block16(b):

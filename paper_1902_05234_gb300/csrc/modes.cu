@@ -103,15 +103,24 @@ __device__ __forceinline__ uint4 shfl_from31(uint4 v) {
                       __shfl_sync(0xffffffffu, v.z, 31), __shfl_sync(0xffffffffu, v.w, 31));
 }
 
-template <int NR, int NB, int LAYOUT>
-__global__ void __launch_bounds__(max_threads_for_nb(NB), 1) cbc_dec_kernel(const __grid_constant__ CbcArgs a) {
+// Decryption of the two chained modes whose decryption is parallel (section
+// 3.1.2-3.1.3, Table 1 marks their encryption unsuitable): each plaintext
+// block needs its ciphertext block C_i and the one before, C_{i-1} (the IV
+// before block 0).
+//   CBC  P_i = D(C_i) xor C_{i-1}   (inverse cipher on the current block)
+//   CFB  P_i = C_i xor E(C_{i-1})   (forward cipher on the previous block)
+enum : int { kChainCbc = 0, kChainCfb = 1 };
+
+template <int MODE, int NR, int NB, int LAYOUT>
+__global__ void __launch_bounds__(max_threads_for_nb(NB), 1) chain_dec_kernel(const __grid_constant__ CbcArgs a) {
+    constexpr int DIR = MODE == kChainCbc ? kDecrypt : kEncrypt;
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t lane = threadIdx.x & 31u;
     const unsigned long long n = a.nblocks;
     const unsigned long long wpc = blockDim.x >> 5;
     const unsigned long long step = static_cast<unsigned long long>(gridDim.x) * wpc * 32ull * NB;
     unsigned long long base = (blockIdx.x * wpc + (threadIdx.x >> 5)) * 32ull * NB;
-    Tab<LAYOUT, kDecrypt>::fill(smem, threadIdx.x, blockDim.x);
+    Tab<LAYOUT, DIR>::fill(smem, threadIdx.x, blockDim.x);
     __syncthreads();
     griddep_release();
     griddep_wait();  // global memory only after this (see aes_kernels.cuh)
@@ -127,7 +136,7 @@ __global__ void __launch_bounds__(max_threads_for_nb(NB), 1) cbc_dec_kernel(cons
         cur[i] = b < n ? ld_block(a.in + b) : make_uint4(0, 0, 0, 0);
     }
     uint4 before_cur = before(base);
-    const Tab<LAYOUT, kDecrypt> tab(smem, lane);
+    const Tab<LAYOUT, DIR> tab(smem, lane);
     const ParamKey key{a.rk.w};
     for (; base < n; base += step) {
         uint4 nxt[NB];
@@ -149,15 +158,15 @@ __global__ void __launch_bounds__(max_threads_for_nb(NB), 1) cbc_dec_kernel(cons
         uint32_t s[NB][4];
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
-            s[i][0] = cur[i].x; s[i][1] = cur[i].y; s[i][2] = cur[i].z; s[i][3] = cur[i].w;
+            const uint4 x = MODE == kChainCbc ? cur[i] : prev[i];  // the block the cipher runs on
+            s[i][0] = x.x; s[i][1] = x.y; s[i][2] = x.z; s[i][3] = x.w;
         }
-        cipher_states<kDecrypt, NR, NB>(tab, key, s);
+        cipher_states<DIR, NR, NB>(tab, key, s);
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
             const unsigned long long b = base + lane + 32ull * i;
-            if (b < n)
-                st_block(a.out + b, make_uint4(prev[i].x ^ s[i][0], prev[i].y ^ s[i][1], prev[i].z ^ s[i][2],
-                                               prev[i].w ^ s[i][3]));
+            const uint4 y = MODE == kChainCbc ? prev[i] : cur[i];  // the block XORed onto its output
+            if (b < n) st_block(a.out + b, make_uint4(y.x ^ s[i][0], y.y ^ s[i][1], y.z ^ s[i][2], y.w ^ s[i][3]));
             cur[i] = nxt[i];
         }
         before_cur = before_nxt;
@@ -166,6 +175,8 @@ __global__ void __launch_bounds__(max_threads_for_nb(NB), 1) cbc_dec_kernel(cons
 
 #define AESGB_M(KERNEL, NR, NB)                                                \
     if (nr == NR && nb == NB) return reinterpret_cast<const void *>(&KERNEL<NR, NB, kLayoutR4>);
+#define AESGB_C(MODE, NR, NB)                                                  \
+    if (nr == NR && nb == NB) return reinterpret_cast<const void *>(&chain_dec_kernel<MODE, NR, NB, kLayoutR4>);
 
 // One block per thread: ECB measures the same at 16 and 32 bytes per thread,
 // and the counter / chaining state would not fit 64 registers at two.
@@ -175,7 +186,12 @@ const void *ctr_kernel_ptr(int nr, int nb) {
 }
 
 const void *cbc_dec_kernel_ptr(int nr, int nb) {
-    AESGB_M(cbc_dec_kernel, 10, 1) AESGB_M(cbc_dec_kernel, 12, 1) AESGB_M(cbc_dec_kernel, 14, 1)
+    AESGB_C(kChainCbc, 10, 1) AESGB_C(kChainCbc, 12, 1) AESGB_C(kChainCbc, 14, 1)
+    return nullptr;
+}
+
+const void *cfb_dec_kernel_ptr(int nr, int nb) {
+    AESGB_C(kChainCfb, 10, 1) AESGB_C(kChainCfb, 12, 1) AESGB_C(kChainCfb, 14, 1)
     return nullptr;
 }
 
@@ -250,6 +266,25 @@ int aes_cbc_decrypt(const uint32_t *rk_dec, int nrounds, const uint8_t *iv, cons
     order_round_keys(kDecrypt, rk_dec, nrounds, &args.rk);
     std::memcpy(&args.iv, iv, 16);
     return launch_mode(cbc_dec_kernel_ptr(nrounds, c.blocks_per_thread), kDecrypt, c, nblocks, args, stream);
+}
+
+int aes_cfb_decrypt(const uint32_t *rk_enc, int nrounds, const uint8_t *iv, const uint8_t *in, uint8_t *out,
+                    size_t nblocks, void *stream) {
+    int st = check_nrounds(nrounds);
+    if (st != AES_OK) return st;
+    if (!rk_enc || !iv) return AES_E_ARG;
+    if (nblocks == 0) return AES_OK;
+    st = check_buffers(in, out, nblocks);
+    if (st != AES_OK) return st;
+    if (in == out) return AES_E_OVERLAP;  // as CBC: C_i is read again after P_i would overwrite it
+    const aes_launch_cfg c = mode_cfg(kEncrypt, nrounds, nblocks);
+    CbcArgs args;
+    args.in = reinterpret_cast<const uint4 *>(in);
+    args.out = reinterpret_cast<uint4 *>(out);
+    args.nblocks = nblocks;
+    order_round_keys(kEncrypt, rk_enc, nrounds, &args.rk);
+    std::memcpy(&args.iv, iv, 16);
+    return launch_mode(cfb_dec_kernel_ptr(nrounds, c.blocks_per_thread), kEncrypt, c, nblocks, args, stream);
 }
 
 }  // extern "C"

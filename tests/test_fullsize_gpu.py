@@ -18,7 +18,7 @@ checked against the oracle, properties over the whole buffer on the device.
   same ciphertext (checked against the oracle on windows) and decrypts it back;
   every batch-tuner candidate gives the same 5.2 GB batch output.
 * 1 GiB through the other kernels the benchmark times: the constant-time
-  kernel (every key size), the TMA-staged layout, CTR and CBC decryption --
+  kernel (every key size), the TMA-staged layout, CTR, CBC and CFB decryption --
   oracle windows, and round trips over the whole buffer.
 """
 import numpy as np
@@ -290,8 +290,8 @@ def test_1gib_tma_staged_windows_and_roundtrip(orc, cfg):
 
 
 @pytest.mark.parametrize("keybits", [128, 256])
-def test_1gib_ctr_and_cbc_decrypt_windows(orc, keybits):
-    """CTR and CBC decryption at the size the benchmark times them (1 GiB):
+def test_1gib_ctr_cbc_cfb_windows(orc, keybits):
+    """CTR, CBC and CFB decryption at the size the benchmark times them (1 GiB):
     windows against the oracle, each started from its own counter block or
     chaining block; CTR applied twice gives the input back."""
     torch = torch_cuda()
@@ -319,3 +319,9 @@ def test_1gib_ctr_and_cbc_decrypt_windows(orc, keybits):
         chain = iv if s == 0 else x[s - 16:s].cpu().numpy()
         exp = orc.cbc_decrypt(key, chain, x[s:s + win].cpu().numpy())
         assert np.array_equal(y[s:s + win].cpu().numpy(), exp), ("cbc", s)
+    aesgb.aes_cfb_decrypt(enc, nr, iv, x, y, n)
+    torch.cuda.synchronize()
+    for s in _windows(nbytes, win, 77):
+        chain = iv if s == 0 else x[s - 16:s].cpu().numpy()
+        exp = orc.cfb_decrypt(key, chain, x[s:s + win].cpu().numpy())
+        assert np.array_equal(y[s:s + win].cpu().numpy(), exp), ("cfb", s)

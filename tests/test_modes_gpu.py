@@ -104,3 +104,40 @@ def test_ecb_host_direct(orc):
     with pytest.raises(aesgb.AesError) as e:
         aesgb.aes_ecb_host_direct(0, enc, nr, pageable, h_out, n, s)
     assert e.value.status == -1
+
+
+@pytest.mark.parametrize("keybits", [128, 192, 256])
+def test_cfb_decrypt_matches_oracle(orc, keybits):
+    """CFB decryption (full-block CFB; the forward cipher on the previous
+    ciphertext block) against the oracle, ragged sizes and several grid
+    passes; in place is refused."""
+    torch = torch_cuda()
+    key = wl.random_key(keybits, 97).tobytes()
+    enc, _, nr = aesgb.aes_expand_key(keybits, key)
+    g = wl.rng(97 + keybits)
+    for n in SIZES + [200_003]:
+        iv = g.integers(0, 256, 16, dtype=np.uint8)
+        ct = wl.random_bytes(16 * n, 98 + n)
+        x = torch.from_numpy(ct).cuda()
+        y = torch.full_like(x, 0x5A)
+        aesgb.aes_cfb_decrypt(enc, nr, iv, x, y, n)
+        torch.cuda.synchronize()
+        assert np.array_equal(y.cpu().numpy(), orc.cfb_decrypt(key, iv, ct)), n
+    with pytest.raises(aesgb.AesError) as e:
+        aesgb.aes_cfb_decrypt(enc, nr, iv, x, x, 16)
+    assert e.value.status == -5
+
+
+def test_cfb_roundtrip_with_oracle_encryption(orc):
+    """Ciphertext made by the oracle's (sequential) CFB encryption decrypts back."""
+    torch = torch_cuda()
+    key = wl.random_key(192, 99).tobytes()
+    enc, _, nr = aesgb.aes_expand_key(192, key)
+    iv = wl.random_bytes(16, 99)
+    pt = wl.random_bytes(16 * 70_001, 100)
+    ct = orc.cfb_encrypt(key, iv, pt)
+    x = torch.from_numpy(ct).cuda()
+    y = torch.empty_like(x)
+    aesgb.aes_cfb_decrypt(enc, nr, iv, x, y, pt.size // 16)
+    torch.cuda.synchronize()
+    assert np.array_equal(y.cpu().numpy(), pt)
