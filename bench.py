@@ -293,8 +293,23 @@ def cpu_baseline(keybits: int, seconds: float = 10.0) -> dict:
     t3 = time.perf_counter()
     o.ecb(0, key, small, nthreads=1)
     single = small.size * 8 / (time.perf_counter() - t3) / 1e9
+    # every key size and direction: all cores on the sample and on 1 MiB, one
+    # thread on 1 MiB (about 10 s more in all)
+    by_key = {}
+    for kb in (128, 192, 256):
+        k = wl.random_key(kb, 92).tobytes()
+        row = {}
+        for d, name in ((0, "enc"), (1, "dec")):
+            cell = {}
+            for label, buf, nt in (("all_cores_sample", data, cores), ("all_cores_1MiB", small, cores),
+                                   ("single_thread_1MiB", small, 1)):
+                t = time.perf_counter()
+                o.ecb(d, k, buf, nthreads=nt)
+                cell[label] = round(buf.size * 8 / (time.perf_counter() - t) / 1e9, 5)
+            row[name] = cell
+        by_key[str(kb)] = row
     return {"value": gbps, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "single_thread_gbps": round(single, 5), "openssl_context": openssl_speed(),
+            "single_thread_gbps": round(single, 5), "by_key": by_key, "openssl_context": openssl_speed(),
             "sample": f"AES-{keybits} ECB encrypt+decrypt of {nbytes:,} bytes (seeded uniform random), "
                       f"{cores} threads, contiguous split",
             "seconds": round(t2 - t0, 3), "enc_s": round(t1 - t0, 3), "dec_s": round(t2 - t1, 3)}
