@@ -17,6 +17,8 @@ checked against the oracle, properties over the whole buffer on the device.
 * 1 GiB, AES-128 (the benchmark's workload): every tuner candidate gives the
   same ciphertext (checked against the oracle on windows) and decrypts it back;
   every batch-tuner candidate gives the same 5.2 GB batch output.
+* the largest single call: 2^32 + 1 blocks (64 GiB + 16 B) in place, windows
+  around block 2^32 against the oracle and back.
 * 1 GiB through the other kernels the benchmark times: the constant-time
   kernel (every key size), the TMA-staged layout, CTR, CBC and CFB decryption --
   oracle windows, and round trips over the whole buffer.
@@ -325,3 +327,28 @@ def test_1gib_ctr_cbc_cfb_windows(orc, keybits):
         chain = iv if s == 0 else x[s - 16:s].cpu().numpy()
         exp = orc.cfb_decrypt(key, chain, x[s:s + win].cpu().numpy())
         assert np.array_equal(y[s:s + win].cpu().numpy(), exp), ("cfb", s)
+
+
+def test_over_2_32_blocks_in_place(orc):
+    """One call over more than 2^32 blocks (2^32 + 1 blocks = 64 GiB + 16 B),
+    in place: the block index is 64-bit end to end.  Windows around block 2^32
+    (byte 2^36), the start and the end against the oracle; decryption in place
+    restores them."""
+    torch = torch_cuda()
+    n = (1 << 32) + 1
+    nbytes = 16 * n
+    buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    _fill_random(torch, buf, 80)
+    key = wl.random_key(128, 80).tobytes()
+    enc, dec, nr = aesgb.aes_expand_key(128, key)
+    w = 32 * 1024
+    starts = [0, (1 << 36) - w // 2, nbytes - w]
+    saved = [(s, buf[s:s + w].cpu().numpy()) for s in starts]
+    aesgb.aes_ecb_encrypt(enc, nr, buf, buf, n)
+    torch.cuda.synchronize()
+    for s, before in saved:
+        assert np.array_equal(buf[s:s + w].cpu().numpy(), orc.ecb(0, key, before, nthreads=16)), s
+    aesgb.aes_ecb_decrypt(dec, nr, buf, buf, n)
+    torch.cuda.synchronize()
+    for s, before in saved:
+        assert np.array_equal(buf[s:s + w].cpu().numpy(), before), s
