@@ -29,8 +29,11 @@ map), computed in the tower field GF((2^4)^2) = GF(16)[y]/(y^2 + y + lambda):
     the forms F_ki . d;
   * bottom layer: phi (tower -> AES field) and, for encryption, the affine
     matrix, with the masks, as an XOR program.
-XOR programs are found by a randomised greedy search that repeatedly names
-the pair or triple of variables whose sharing saves the most gates.
+XOR programs come from a closure construction that builds every target as
+the XOR of at most three signals already available -- one gate per target,
+the lower bound, when it reaches all of them -- or else from a randomised
+greedy search that repeatedly names the pair or triple of variables whose
+sharing saves the most gates.
 
 The tower (GF(16) modulus, lambda) and the isomorphism are parameters; the
 defaults were chosen by `--search`, which tries every irreducible quartic,
@@ -38,7 +41,7 @@ every lambda of trace 1 and every isomorphism and keeps the cheapest.
 
 Usage:  python gen_bitslice.py            # writes bitslice_circuits.h
         python gen_bitslice.py --check    # exit 1 if the header is stale
-        python gen_bitslice.py --search   # print the cost of every tower
+        python gen_bitslice.py --search   # print the cost of every tower (about an hour)
 """
 import argparse
 import itertools
@@ -289,10 +292,49 @@ def greedy_plan(nin, rows, rng, noise):
     return defs, rows
 
 
+def closure_plan(nin, masks):
+    """One gate per distinct target: repeatedly build a target that is the
+    XOR of at most three signals already available (inputs and targets built
+    before).  That meets the lower bound of one gate per target that is not an
+    input; returns [(mask, (vars...))] in build order, or None if some target
+    never becomes reachable this way."""
+    avail = {1 << j: j for j in range(nin)}
+    pending = sorted({m for m in masks if m not in avail})
+    plan = []
+    nv = nin
+    while pending:
+        items = sorted(avail.items())
+        pairs = {}
+        for (ma, va), (mb, vb) in itertools.combinations(items, 2):
+            pairs.setdefault(ma ^ mb, (va, vb))
+        hit = None
+        for t in pending:
+            if t in pairs:
+                hit = (t, pairs[t])
+                break
+            for ma, va in items:
+                r = pairs.get(t ^ ma)
+                if r is not None and va not in r:
+                    hit = (t, (va,) + r)
+                    break
+            if hit:
+                break
+        if hit is None:
+            return None
+        t, vs = hit
+        plan.append((t, vs))
+        avail[t] = nv
+        nv += 1
+        pending.remove(t)
+    return plan
+
+
 def xor_program(C, ins, targets, restarts, seed):
     """ins: signals; targets: list of (mask over ins, const).  Adds the gates of
-    the cheapest plan found and returns one signal per target."""
+    the cheapest plan found (the closure construction when it reaches its
+    lower bound, else the greedy search) and returns one signal per target."""
     nin = len(ins)
+    plan = closure_plan(nin, [m for m, _ in targets])
     rows = [[i for i in range(nin) if (m >> i) & 1] for m, _ in targets]
     rng = random.Random(seed)
     best = None
@@ -301,6 +343,14 @@ def xor_program(C, ins, targets, restarts, seed):
         cost = len(defs) + sum(_row_cost(len(f)) for f in fin)
         if best is None or cost < best[0]:
             best = (cost, defs, fin)
+    if plan is not None and len(plan) < best[0]:
+        sig_of = list(ins)  # plan variable -> signal: the inputs, then the targets in build order
+        by_mask = {1 << j: ins[j] for j in range(nin)}
+        for t, vs in plan:
+            g = C.xor([sig_of[v] for v in vs])
+            sig_of.append(g)
+            by_mask[t] = g
+        return [(by_mask[m][0], by_mask[m][1] ^ const) for m, const in targets]
     _, defs, fin = best
     sig = list(ins)
     for d in defs:
