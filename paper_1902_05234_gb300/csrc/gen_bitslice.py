@@ -296,34 +296,42 @@ def closure_plan(nin, masks):
     """One gate per distinct target: repeatedly build a target that is the
     XOR of at most three signals already available (inputs and targets built
     before).  That meets the lower bound of one gate per target that is not an
-    input; returns [(mask, (vars...))] in build order, or None if some target
-    never becomes reachable this way."""
+    input.  Of the targets reachable at each step, the one whose shallowest
+    decomposition is shallowest is built first, so the circuit stays shallow.
+    Returns [(mask, (vars...))] in build order, or None if some target never
+    becomes reachable this way."""
     avail = {1 << j: j for j in range(nin)}
+    depth = {j: 0 for j in range(nin)}
     pending = sorted({m for m in masks if m not in avail})
     plan = []
     nv = nin
     while pending:
         items = sorted(avail.items())
-        pairs = {}
+        pairs = {}  # xor of two available signals -> the shallowest such pair
         for (ma, va), (mb, vb) in itertools.combinations(items, 2):
-            pairs.setdefault(ma ^ mb, (va, vb))
-        hit = None
+            x = ma ^ mb
+            d = max(depth[va], depth[vb])
+            if x not in pairs or d < pairs[x][0]:
+                pairs[x] = (d, (va, vb))
+        hit = None  # (depth, target, vars)
         for t in pending:
+            best = None
             if t in pairs:
-                hit = (t, pairs[t])
-                break
+                best = (pairs[t][0] + 1, pairs[t][1])
             for ma, va in items:
                 r = pairs.get(t ^ ma)
-                if r is not None and va not in r:
-                    hit = (t, (va,) + r)
-                    break
-            if hit:
-                break
+                if r is not None and va not in r[1]:
+                    d = max(depth[va], r[0]) + 1
+                    if best is None or d < best[0]:
+                        best = (d, (va,) + r[1])
+            if best is not None and (hit is None or best[0] < hit[0]):
+                hit = (best[0], t, best[1])
         if hit is None:
             return None
-        t, vs = hit
+        d, t, vs = hit
         plan.append((t, vs))
         avail[t] = nv
+        depth[nv] = d
         nv += 1
         pending.remove(t)
     return plan
