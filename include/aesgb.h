@@ -31,6 +31,11 @@
  *    not stream work).  Make one call of each configuration before capturing
  *    the enqueuing calls into a graph; after that they only enqueue kernels.
  *    aes_batch_graph_create does this set-up itself.
+ *  - Launch overlap: the single-buffer kernels are launched with
+ *    programmatic stream serialisation, so one may start (fill its tables)
+ *    while the previous kernel in the stream drains; it waits for that
+ *    kernel to complete before touching global memory, so stream order
+ *    semantics are unchanged.
  *  - Thread safety: calls may come from several host threads on distinct
  *    streams; library state (caches, tuned configurations, internal streams)
  *    is guarded.  A server handle is the exception (see aes_srv_create).
@@ -137,7 +142,8 @@ typedef enum aes_layout {
     AES_LAYOUT_R1 = 1,    /* 1 table per bank-replicated + byte rotations: 64 KiB  */
     AES_LAYOUT_P4 = 2,    /* 4 plain 1 KiB tables in shared memory (bank conflicts) */
     AES_LAYOUT_CONST = 3, /* tables in constant memory, as in the paper (4.2)      */
-    AES_LAYOUT_R4_TMA = 4 /* R4 tables; the plaintext staged into shared memory by
+    AES_LAYOUT_R4_TMA = 4 /* (plaintext placement, section 4.4) R4 tables; the
+                             plaintext staged into shared memory by
                              TMA bulk copies (two 512 x blocks_per_thread-byte
                              tiles per warp, mbarrier-tracked, two passes ahead)
                              instead of loaded into registers                     */
