@@ -64,6 +64,7 @@ def parse_args():
     p.add_argument("--no-stress", action="store_true")
     p.add_argument("--no-ct", action="store_true", help="skip the constant-time (bitsliced) kernel")
     p.add_argument("--served-requests", type=int, default=20000)
+    p.add_argument("--served-slots", type=int, default=4, help="in-flight batch slots of the served section's server")
     p.add_argument("--batch-n", type=int, default=4096, help="messages in the batched workload")
     p.add_argument("--batch-max-bytes", type=int, default=16 * MIB, help="largest message of the batched workload")
     p.add_argument("--study", action="store_true",
@@ -529,7 +530,7 @@ def batch_roofline(batched, n, hi, sms, f_mhz):
             "peak_basis": f"{sms} SMs x {f_mhz:.0f} MHz x 128 B/clk over 64 Nr + 32 B per block of each message"}
 
 
-def run_served(torch, aesgb, dev, n_req=20000, loads=(0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9, 1.0)):
+def run_served(torch, aesgb, dev, n_req=20000, loads=(0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9, 1.0), slots=4):
     """Served workload: a Poisson stream of encrypt/decrypt requests, sizes
     log-uniform 64 B .. 4 MiB, keys drawn from 1,024 resident schedules,
     direction 50/50, through the continuous-batching server under a 4 GiB
@@ -549,7 +550,7 @@ def run_served(torch, aesgb, dev, n_req=20000, loads=(0.1, 0.2, 0.3, 0.4, 0.5, 0
     dst = torch.empty_like(src)
     ins = src.data_ptr() + offs[:-1].astype(np.uint64)
     outs = dst.data_ptr() + offs[:-1].astype(np.uint64)
-    srv = aesgb.aes_srv_create(4 << 30, 1024, max_batch=8192, slots=4)
+    srv = aesgb.aes_srv_create(4 << 30, 1024, max_batch=8192, slots=slots)
     try:
         kg = wl.rng(61)
         host_keys = []
@@ -598,7 +599,7 @@ def run_served(torch, aesgb, dev, n_req=20000, loads=(0.1, 0.2, 0.3, 0.4, 0.5, 0
     loop = served_loop_baseline(torch, aesgb, src, ref, offs, sizes, key_ids, dirs, host_keys)
     out = {"workload": f"{n_req} requests per load point, Poisson arrivals, sizes log-uniform 64 B..4 MiB "
                        f"(total {total:,} B), 1,024 resident keys (128/192/256), direction 50/50, "
-                       f"4 GiB budget, 4 in-flight batches",
+                       f"4 GiB budget, {slots} in-flight batches",
            "peak_gbps": round(peak_bps * 8 / 1e9, 1), "sweep": rows,
            "submit_many_ms": round(statistics.median(submit_ms), 3),
            "identical_across_loads": identical, "batches_total": stats["batches"],
@@ -987,7 +988,7 @@ def run_gb300(args, dist: Dist):
     if dist.rank == 0 and world == 1 and not args.no_stress:
         line["stress"] = run_stress(torch, aesgb, dev)
     if dist.rank == 0 and world == 1 and not args.no_served:
-        line["served"] = run_served(torch, aesgb, dev, n_req=args.served_requests)
+        line["served"] = run_served(torch, aesgb, dev, n_req=args.served_requests, slots=args.served_slots)
     if dist.rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.keybits)
     if dist.rank == 0:
