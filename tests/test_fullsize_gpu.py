@@ -17,6 +17,8 @@ checked against the oracle, properties over the whole buffer on the device.
 * 1 GiB, AES-128 (the benchmark's workload): every tuner candidate gives the
   same ciphertext (checked against the oracle on windows) and decrypts it back;
   every batch-tuner candidate gives the same 5.2 GB batch output.
+* the single-buffer sweep, 1 MiB .. 1 GiB, every key size, both directions:
+  whole outputs against the oracle up to 64 MiB, 1 MiB windows above.
 * the largest single call: 2^32 + 1 blocks (64 GiB + 16 B) in place, windows
   around block 2^32 against the oracle and back.
 * 1 GiB through the other kernels the benchmark times: the constant-time
@@ -352,3 +354,40 @@ def test_over_2_32_blocks_in_place(orc):
     torch.cuda.synchronize()
     for s, before in saved:
         assert np.array_equal(buf[s:s + w].cpu().numpy(), before), s
+
+
+@pytest.mark.parametrize("keybits", [128, 192, 256])
+def test_single_buffer_sweep_parity(orc, keybits):
+    """The single-buffer sweep's sizes (1 MiB .. 1 GiB in powers of 4; 4 GiB is
+    the test above) in both directions, default launch configuration: the
+    whole output against the oracle up to 64 MiB; above that 16 random 1 MiB
+    windows plus the first and the last, and decryption back over the whole
+    buffer."""
+    torch = torch_cuda()
+    key = wl.random_key(keybits, 90).tobytes()
+    enc, dec, nr = aesgb.aes_expand_key(keybits, key)
+    g = wl.rng(90 + keybits)
+    for mib in (1, 4, 16, 64, 256, 1024):
+        nbytes = mib * MIB
+        n = nbytes // 16
+        x = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        _fill_random(torch, x, 91 + mib)
+        y = torch.empty_like(x)
+        z = torch.empty_like(x)
+        aesgb.aes_ecb_encrypt(enc, nr, x, y, n)
+        aesgb.aes_ecb_decrypt(dec, nr, x, z, n)
+        torch.cuda.synchronize()
+        if mib <= 64:
+            xh = x.cpu().numpy()
+            assert np.array_equal(y.cpu().numpy(), orc.ecb(0, key, xh, nthreads=16)), (mib, "enc")
+            assert np.array_equal(z.cpu().numpy(), orc.ecb(1, key, xh, nthreads=16)), (mib, "dec")
+        else:
+            starts = [0, nbytes - MIB] + [int(v) // 16 * 16 for v in g.integers(0, nbytes - MIB, 16)]
+            for s in starts:
+                xw = x[s:s + MIB].cpu().numpy()
+                assert np.array_equal(y[s:s + MIB].cpu().numpy(), orc.ecb(0, key, xw, nthreads=16)), (mib, s)
+                assert np.array_equal(z[s:s + MIB].cpu().numpy(), orc.ecb(1, key, xw, nthreads=16)), (mib, s)
+            aesgb.aes_ecb_decrypt(dec, nr, y, y, n)
+            torch.cuda.synchronize()
+            assert torch.equal(x, y), mib
+        del x, y, z
