@@ -3,8 +3,8 @@ benchmark times: the library's default for the size and every candidate the
 autotuner can pick (the benchmark tunes before timing).  Sampled windows are
 checked against the oracle, properties over the whole buffer on the device.
 
-* single buffers of 4 GiB, AES-128/192/256: 10 windows of 256 KiB (first, last,
-  eight seeded random) against the oracle; decrypt(encrypt(x)) == x over all
+* single buffers of 4 GiB, AES-128/192/256: 18 windows of 1 MiB (first, last,
+  16 seeded random) against the oracle; decrypt(encrypt(x)) == x over all
   4 GiB on the device.
 * the 4,096-message batch (5.2 GB): every message equal to the single-buffer
   path; all messages up to 16 KiB and a 4 KiB window of every 8th larger one
@@ -56,9 +56,9 @@ def test_4gib_single_buffer_windows_and_roundtrip(orc, keybits):
     enc, dec, nr = aesgb.aes_expand_key(keybits, key)
     aesgb.aes_ecb_encrypt(enc, nr, x, y, n)
     torch.cuda.synchronize()
-    win = 256 * 1024
+    win = MIB
     g = wl.rng(51)
-    starts = [0, nbytes - win] + [int(v) // 16 * 16 for v in g.integers(0, nbytes - win, 8)]
+    starts = [0, nbytes - win] + [int(v) // 16 * 16 for v in g.integers(0, nbytes - win, 16)]
     for s in starts:
         got = y[s:s + win].cpu().numpy()
         exp = orc.ecb(0, key, x[s:s + win].cpu().numpy(), nthreads=16)
