@@ -7,8 +7,8 @@ checked against the oracle, properties over the whole buffer on the device.
   16 seeded random) against the oracle; decrypt(encrypt(x)) == x over all
   4 GiB on the device.
 * the 4,096-message batch (5.2 GB): every message equal to the single-buffer
-  path; all messages up to 16 KiB and a 4 KiB window of every 8th larger one
-  against the oracle.
+  path; every message up to 64 KiB, and the first and last 2 KiB of every
+  larger one, against the oracle.
 * the stress case: AES-256 decryption in place over 16 GiB of 64 MiB regions
   cycling uniform random / all-zero / one block repeated; 32 windows of 1 MiB
   (region boundaries included) against the oracle, and every all-zero or
@@ -102,19 +102,19 @@ def test_batch_4096_messages_fullsize(orc):
     torch.cuda.synchronize()
     assert bool((status == 0).all())
     assert torch.equal(dst, ref)
+    src_h = src.cpu().numpy()
+    dst_h = dst.cpu().numpy()
     for i in range(n):
         ln = int(lengths[i])
         o = int(offs[i])
-        if ln <= 16 * 1024:
-            m = src[o:o + ln].cpu().numpy()
-            exp = orc.ecb(int(dirs[i]), keys[i], m, nthreads=1)
-            assert np.array_equal(dst[o:o + ln].cpu().numpy(), exp), i
-        elif i % 8 == 0:
-            w = 4096
-            s = o + (ln - w) // 2 // 16 * 16
-            m = src[s:s + w].cpu().numpy()
-            exp = orc.ecb(int(dirs[i]), keys[i], m, nthreads=1)
-            assert np.array_equal(dst[s:s + w].cpu().numpy(), exp), i
+        if ln <= 64 * 1024:
+            exp = orc.ecb(int(dirs[i]), keys[i], src_h[o:o + ln], nthreads=1)
+            assert np.array_equal(dst_h[o:o + ln], exp), i
+        else:
+            w = 2048
+            for s in (o, o + ln - w):  # the first and the last 2 KiB of the message
+                exp = orc.ecb(int(dirs[i]), keys[i], src_h[s:s + w], nthreads=1)
+                assert np.array_equal(dst_h[s:s + w], exp), (i, s)
 
 
 def test_stress_16gib_aes256_decrypt_in_place(orc):
