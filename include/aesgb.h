@@ -83,6 +83,25 @@ int aes_version(void);
  * from the counter). */
 int aes_wait_timeouts(unsigned long long *count);
 
+/* Debug build only (libaesgb_debug.so, compiled with AESGB_BOUNDS_CHECK):
+ * the number of index checks that failed in any kernel since the last call,
+ * summed over the kernels' translation units; reading resets it.  The debug
+ * build checks every shared-memory table, tile, mask and key-slot access and
+ * the global ranges the batch and TMA kernels derive on the device; a failed
+ * check is counted and its access skipped (nothing traps).  AES_E_CONFIG with
+ * *count = 0 in the release build.  DEVICE-synchronous. */
+int aes_debug_bounds_violations(unsigned long long *count);
+
+/* Debug build only: exactly-once coverage of the batch kernel's work counter.
+ * Each chunk (chunk_blocks consecutive blocks of one message, the unit a warp
+ * takes from the counter) adds one to its tag, for chunk indices below 65,536.
+ * Returns, over all batch launches since the last call: *once the chunks
+ * tagged exactly once, *repeated those tagged more than once, *beyond the
+ * chunks whose index lies past the tags; then clears the tags.  After ONE
+ * launch of T <= 65,536 chunks, *once == T and the others are 0.
+ * AES_E_CONFIG with all three 0 in the release build.  DEVICE-synchronous. */
+int aes_debug_batch_coverage(unsigned long long *once, unsigned long long *repeated, unsigned long long *beyond);
+
 /* Failure-detection test hook: one warp of the TMA-staged encryption kernel
  * on nblocks (1..64) DEVICE blocks, with every mbarrier expecting 16 bytes
  * more than its bulk copy delivers.  The copies land, but no wait can finish:

@@ -19,7 +19,10 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libaesgb.so")
+# AESGB_LIBRARY=debug loads the bounds-checking build (libaesgb_debug.so, made
+# by ``build(debug=True)``) instead of the release library.
+LIB_PATH = os.path.join(_HERE, "libaesgb_debug.so" if os.environ.get("AESGB_LIBRARY") == "debug"
+                        else "libaesgb.so")
 
 _lib = None
 _lock = threading.Lock()
@@ -112,6 +115,8 @@ _SIGNATURES = {
     "aes_ct_ops_per_block": (_i, [_i, _i, ctypes.POINTER(ctypes.c_double)]),
     "aes_wait_timeouts": (_i, [ctypes.POINTER(ctypes.c_ulonglong)]),
     "aes_tma_selftest_timeout": (_i, [_vp, _vp, _sz, _vp]),
+    "aes_debug_bounds_violations": (_i, [ctypes.POINTER(ctypes.c_ulonglong)]),
+    "aes_debug_batch_coverage": (_i, [ctypes.POINTER(ctypes.c_ulonglong)] * 3),
     "aes_ctr_crypt": (_i, [_u32p, _i, _u8p, _vp, _vp, _sz, _vp]),
     "aes_cbc_decrypt": (_i, [_u32p, _i, _u8p, _vp, _vp, _sz, _vp]),
     "aes_cfb_decrypt": (_i, [_u32p, _i, _u8p, _vp, _vp, _sz, _vp]),
@@ -418,6 +423,23 @@ def aes_wait_timeouts() -> int:
     v = ctypes.c_ulonglong()
     _check(lib().aes_wait_timeouts(ctypes.byref(v)), "aes_wait_timeouts")
     return v.value
+
+
+def aes_debug_bounds_violations() -> int:
+    """Failed index checks since the last call (debug library only; reading resets it).
+
+    Raises AesError (AES_E_CONFIG) when the loaded library is the release build.
+    """
+    v = ctypes.c_ulonglong()
+    _check(lib().aes_debug_bounds_violations(ctypes.byref(v)), "aes_debug_bounds_violations")
+    return v.value
+
+
+def aes_debug_batch_coverage() -> tuple[int, int, int]:
+    """(chunks taken once, more than once, past the tags) since the last call (debug library only)."""
+    v = [ctypes.c_ulonglong() for _ in range(3)]
+    _check(lib().aes_debug_batch_coverage(*[ctypes.byref(x) for x in v]), "aes_debug_batch_coverage")
+    return v[0].value, v[1].value, v[2].value
 
 
 def aes_tma_selftest_timeout(in_, out, nblocks: int, stream=None) -> None:

@@ -36,6 +36,7 @@
 #include <cuda_runtime.h>
 
 #include "aes_tables.h"
+#include "bounds.cuh"
 
 namespace aesgb {
 
@@ -69,10 +70,14 @@ constexpr int max_threads_for_nb(int nb) { return nb >= 4 ? 512 : 1024; }
 // Each module keeps its own copy of the compile-time tables in constant memory.
 static __constant__ ConstTables c_tab = make_const_tables();
 
+// Table reads and writes at a byte offset into the dynamic shared memory
+// (checked against the launch's size in the debug build).
 __device__ __forceinline__ uint32_t lds32(const uint8_t *smem, uint32_t off) {
+    if (!AESGB_CHECK(off + 4u <= dyn_smem_bytes())) return 0u;
     return *reinterpret_cast<const uint32_t *>(smem + off);
 }
 __device__ __forceinline__ void sts32(uint8_t *smem, uint32_t off, uint32_t v) {
+    if (!AESGB_CHECK(off + 4u <= dyn_smem_bytes())) return;
     *reinterpret_cast<uint32_t *>(smem + off) = v;
 }
 __device__ __forceinline__ uint32_t rotl32(uint32_t v, int n) {

@@ -32,6 +32,7 @@
 #include "aes_kernels.cuh"
 #include "batch_internal.h"
 #include "capi_internal.h"
+#include "registry.h"
 
 namespace aesgb {
 
@@ -216,6 +217,15 @@ struct BatchArgs {
 
 constexpr uint32_t kKeySlotBytes = 256;  // 60 words rounded up
 
+#if defined(AESGB_BOUNDS_CHECK)
+// Debug build: every chunk a warp takes adds one to its tag, so that after one
+// launch each of the T chunks must carry exactly 1 (aes_debug_batch_coverage
+// reads and clears the tags).  Chunks past the array are counted in bulk.
+constexpr unsigned int kTagChunks = 1u << 16;
+static __device__ unsigned int g_chunk_tag[kTagChunks];
+static __device__ unsigned long long g_chunk_tag_beyond;
+#endif
+
 // Round keys of the current message held in registers for a whole chunk
 // (4*(NR+1) words; every index is a compile-time constant once the rounds
 // are unrolled, so the array stays in registers).
@@ -306,6 +316,10 @@ __device__ void batch_phase(const BatchArgs &a, const WsView &v, uint8_t *smem, 
     int nr = 10;
     bool have = false;
     unsigned long long ticket = 0;
+    // the warp's key slot lies inside the launch's shared memory
+    if (!AESGB_CHECK(static_cast<uint32_t>(reinterpret_cast<uint8_t *>(kslot) - smem) + kKeySlotBytes <=
+                     dyn_smem_bytes()))
+        return;
     if (lane == 0) ticket = atomicAdd(counter, 1ull);
     unsigned long long rel = __shfl_sync(0xffffffffu, ticket, 0);
     while (rel < nchunks) {
@@ -313,6 +327,11 @@ __device__ void batch_phase(const BatchArgs &a, const WsView &v, uint8_t *smem, 
         const unsigned long long c = c_begin + rel;
         if (!have || c >= p_end) {
             p = find_message(v.start, have ? p + 1 : 0, n, c, lane);
+            // p is a partition position with c in its chunk range, and names
+            // a message (each value is the same in every lane: no divergence)
+            if (!AESGB_CHECK(p >= 0 && p < n && v.order[p] < static_cast<uint32_t>(n) && v.start[p] <= c &&
+                             c < v.start[p + 1]))
+                break;
             p_start = v.start[p];
             p_end = v.start[p + 1];
             const aes_desc d = a.desc[v.order[p]];
@@ -332,6 +351,13 @@ __device__ void batch_phase(const BatchArgs &a, const WsView &v, uint8_t *smem, 
         }
         const unsigned long long first = (c - p_start) * cb;
         const unsigned long long cnt = nb - first < cb ? nb - first : cb;
+        if (!AESGB_CHECK(first < nb && cnt >= 1 && cnt <= cb && (nr == 10 || nr == 12 || nr == 14))) break;
+#if defined(AESGB_BOUNDS_CHECK)
+        if (lane == 0) {
+            if (c < kTagChunks) atomicAdd(&g_chunk_tag[c], 1u);
+            else atomicAdd(&g_chunk_tag_beyond, 1ull);
+        }
+#endif
         switch (nr) {
         case 10: batch_chunk<DIR, 10, NB>(tab, kslot, in, out, first, cnt, lane); break;
         case 12: batch_chunk<DIR, 12, NB>(tab, kslot, in, out, first, cnt, lane); break;
@@ -362,6 +388,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(const __grid
         batch_phase<kDecrypt, NB>(a, v, smem, kslot, E, T);
     }
 }
+
+AESGB_BOUNDS_READER(batch)
 
 uint32_t batch_smem_bytes(int threads) {
     return table_smem_bytes(kDecrypt, kLayoutR4) + static_cast<uint32_t>(threads / 32) * kKeySlotBytes;
@@ -560,6 +588,39 @@ int noalloc_scratch_ptr(int dev, void **out) {
     return AES_OK;
 }
 
+// Debug build: counts of chunks taken exactly once and more than once since
+// the last call, and of chunks past the tag array; clears the tags.
+int read_chunk_coverage(unsigned long long *once, unsigned long long *repeated, unsigned long long *beyond) {
+#if defined(AESGB_BOUNDS_CHECK)
+    static unsigned int tags[kTagChunks];
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    const unsigned long long zero = 0;
+    if (cudaMemcpyFromSymbol(tags, g_chunk_tag, sizeof tags) != cudaSuccess ||
+        cudaMemcpyFromSymbol(beyond, g_chunk_tag_beyond, sizeof *beyond) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return AES_E_CUDA;
+    }
+    *once = 0;
+    *repeated = 0;
+    for (unsigned int i = 0; i < kTagChunks; ++i) {
+        *once += tags[i] == 1;
+        *repeated += tags[i] > 1;
+    }
+    void *tag_addr = nullptr;
+    if (cudaGetSymbolAddress(&tag_addr, g_chunk_tag) != cudaSuccess ||
+        cudaMemset(tag_addr, 0, sizeof tags) != cudaSuccess ||
+        cudaMemcpyToSymbol(g_chunk_tag_beyond, &zero, sizeof zero) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return AES_E_CUDA;
+    }
+    return AES_OK;
+#else
+    *once = *repeated = *beyond = 0;
+    return AES_E_CONFIG;
+#endif
+}
+
 }  // namespace aesgb
 
 using namespace aesgb;
@@ -567,6 +628,11 @@ using namespace aesgb;
 extern "C" {
 
 size_t aes_batch_workspace_bytes(int n) { return n < 0 ? 0 : batch_ws_bytes(n); }
+
+int aes_debug_batch_coverage(unsigned long long *once, unsigned long long *repeated, unsigned long long *beyond) {
+    if (!once || !repeated || !beyond) return AES_E_ARG;
+    return read_chunk_coverage(once, repeated, beyond);
+}
 
 int aes_ecb_batch_ws(const aes_desc *desc_dev, int n, void *ws, size_t ws_bytes, int32_t *status_dev,
                      const aes_batch_cfg *cfg, void *stream) {

@@ -206,6 +206,25 @@ int aes_wait_timeouts(unsigned long long *count) {
     return read_wait_timeouts(count);
 }
 
+int aes_debug_bounds_violations(unsigned long long *count) {
+    if (!count) return AES_E_ARG;
+    *count = 0;
+#if defined(AESGB_BOUNDS_CHECK)
+    int (*const readers[])(unsigned long long *) = {bounds_violations_ecb_enc, bounds_violations_ecb_dec,
+                                                     bounds_violations_ecb_tma, bounds_violations_modes,
+                                                     bounds_violations_batch,   bounds_violations_ct};
+    for (auto rd : readers) {
+        unsigned long long v = 0;
+        const int st = rd(&v);
+        if (st != AES_OK) return st;
+        *count += v;
+    }
+    return AES_OK;
+#else
+    return AES_E_CONFIG;
+#endif
+}
+
 int aes_tma_selftest_timeout(const uint8_t *in, uint8_t *out, size_t nblocks, void *stream) {
     if (nblocks == 0 || nblocks > 64) return AES_E_RANGE;
     const int st = check_buffers(in, out, nblocks);

@@ -16,6 +16,7 @@
 #include "aes_kernels.cuh"
 #include "bitslice.cuh"
 #include "capi_internal.h"
+#include "registry.h"
 
 namespace aesgb {
 
@@ -79,6 +80,9 @@ void build_masks(int dir, const uint32_t *rk, int nr, uint8_t (*out)[16]) {
 // Mask byte -> 8 planes, in the state's layout (plane 8r + b of column c).
 AESGB_HD void expand_mask(const uint8_t (*m)[16], int i, bs::RoundMasks *dst) {
     const int app = i >> 7, p = i & 127, c = p >> 5, rb = p & 31;
+#if defined(__CUDA_ARCH__)
+    if (!AESGB_CHECK(app < 15)) return;
+#endif
     dst[app].m[c][rb] = ((m[app][(rb >> 3) + 4 * c] >> (rb & 7)) & 1) ? 0xffffffffu : 0u;
 }
 
@@ -116,6 +120,8 @@ __global__ void __launch_bounds__(kCtThreads, 1) ct_kernel(const __grid_constant
         }
     }
 }
+
+AESGB_BOUNDS_READER(ct)
 
 }  // namespace aesgb
 

@@ -13,6 +13,8 @@ namespace aesgb {
     AESGB_K(NR, 1, kLayoutR1) AESGB_K(NR, 2, kLayoutR1) AESGB_K(NR, 4, kLayoutR1) \
     AESGB_K(NR, 1, kLayoutP4) AESGB_K(NR, 1, kLayoutConst)
 
+AESGB_BOUNDS_READER(ecb_enc)
+
 const void *ecb_kernel_enc(int nr, int nb, int layout) {
     AESGB_NR(10)
     AESGB_NR(12)

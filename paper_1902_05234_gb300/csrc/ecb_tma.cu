@@ -90,6 +90,10 @@ __global__ void __launch_bounds__(max_threads_for_nb(NB), 1)
         if (b >= n) return;
         const unsigned long long cnt = n - b < kTileBlocks ? n - b : kTileBlocks;
         const uint32_t bytes = static_cast<uint32_t>(cnt * 16ull);
+        // the copy stays inside the input and inside this warp's tile
+        if (!AESGB_CHECK(b + cnt <= n && cnt >= 1 && cnt <= kTileBlocks &&
+                         static_cast<uint32_t>(stage - smem) + (buf + 1) * kTile <= dyn_smem_bytes()))
+            return;
         mbar_arrive_expect_tx(&bar[buf], bytes + extra_tx);
         bulk_load(stage + buf * kTile, a.in + b, bytes, &bar[buf]);
     };
@@ -123,7 +127,9 @@ __global__ void __launch_bounds__(max_threads_for_nb(NB), 1)
         uint32_t s[NB][4];
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
-            const uint4 v = *reinterpret_cast<const uint4 *>(stage + buf * kTile + (lane + 32u * i) * 16u);
+            const uint32_t at = buf * kTile + (lane + 32u * i) * 16u;
+            (void)AESGB_CHECK(at + 16u <= kTile * 2u);
+            const uint4 v = *reinterpret_cast<const uint4 *>(stage + at);
             s[i][0] = v.x; s[i][1] = v.y; s[i][2] = v.z; s[i][3] = v.w;
         }
         __syncwarp();  // every lane has read the tile before it is refilled
@@ -146,6 +152,8 @@ __global__ void __launch_bounds__(max_threads_for_nb(NB), 1)
             if (base + k * step < n) (void)mbar_wait_bounded(&bar[(it + k) & 1u], ((it + k) >> 1) & 1u);
     }
 }
+
+AESGB_BOUNDS_READER(ecb_tma)
 
 #define AESGB_TMA(D, NR, NB)                                                     \
     if (dir == D && nr == NR && nb == NB)                                        \

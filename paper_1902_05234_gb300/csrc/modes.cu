@@ -19,6 +19,7 @@
 
 #include "aes_kernels.cuh"
 #include "capi_internal.h"
+#include "registry.h"
 
 namespace aesgb {
 
@@ -127,7 +128,9 @@ __global__ void __launch_bounds__(max_threads_for_nb(NB), 1) chain_dec_kernel(co
     // the ciphertext block just before a slice (lane 0's chaining value; the
     // IV before block 0), loaded one pass ahead like the slice itself
     auto before = [&](unsigned long long b) {
-        return b == 0 ? a.iv : (lane == 0 && b < n ? ld_block(a.in + (b - 1)) : make_uint4(0, 0, 0, 0));
+        return b == 0 ? a.iv
+                      : (lane == 0 && b < n && AESGB_CHECK(b - 1 < n) ? ld_block(a.in + (b - 1))
+                                                                       : make_uint4(0, 0, 0, 0));
     };
     uint4 cur[NB];
 #pragma unroll
@@ -172,6 +175,8 @@ __global__ void __launch_bounds__(max_threads_for_nb(NB), 1) chain_dec_kernel(co
         before_cur = before_nxt;
     }
 }
+
+AESGB_BOUNDS_READER(modes)
 
 #define AESGB_M(KERNEL, NR, NB)                                                \
     if (nr == NR && nb == NB) return reinterpret_cast<const void *>(&KERNEL<NR, NB, kLayoutR4>);

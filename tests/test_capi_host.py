@@ -86,6 +86,18 @@ def test_argument_checks_before_cuda(lib):
     assert lib.aes_ecb_crypt_cfg(2, rk, 10, A, A + 4096, 4, ctypes.byref(aesgb.make_cfg()), None) == -1
 
 
+def test_debug_counter_is_debug_build_only(lib):
+    """The release library has no index checks: its counter entry point
+    answers AES_E_CONFIG (with a zero count) without touching the device."""
+    v = ctypes.c_ulonglong(7)
+    assert lib.aes_debug_bounds_violations(ctypes.byref(v)) == -12
+    assert v.value == 0
+    assert lib.aes_debug_bounds_violations(None) == -1
+    c = [ctypes.c_ulonglong(7) for _ in range(3)]
+    assert lib.aes_debug_batch_coverage(*[ctypes.byref(x) for x in c]) == -12
+    assert [x.value for x in c] == [0, 0, 0]
+
+
 def test_default_cfg_is_valid():
     for d in (0, 1):
         for nr in (10, 12, 14):
