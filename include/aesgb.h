@@ -66,7 +66,9 @@ typedef enum aes_status {
     AES_E_BUSY = -9,     /* admission refused: budget or slots full            */
     AES_E_RANGE = -10,   /* a size above a documented maximum                  */
     AES_E_NOTFOUND = -11,/* unknown key id or ticket                           */
-    AES_E_CONFIG = -12   /* launch configuration not supported                 */
+    AES_E_CONFIG = -12,  /* launch configuration not supported                 */
+    AES_E_CANCELLED = -13,   /* a server request cancelled before its launch   */
+    AES_E_UNREGISTERED = -14 /* a server buffer outside every registered range */
 } aes_status;
 
 /* Name of a status code (static string; "unknown status" for other values). */
@@ -91,6 +93,15 @@ int aes_wait_timeouts(unsigned long long *count);
  * check is counted and its access skipped (nothing traps).  AES_E_CONFIG with
  * *count = 0 in the release build.  DEVICE-synchronous. */
 int aes_debug_bounds_violations(unsigned long long *count);
+
+/* Failure-injection test hook (host side, every build).  Of the memory
+ * allocations the library makes for itself from now on -- the device and
+ * page-locked host memory of aes_srv_create, the library-owned batch
+ * workspace of aes_ecb_batch -- the first `skip` succeed and the `count`
+ * after them fail as if the device were out of memory, so that each caller's
+ * AES_E_NOMEM path and its clean-up run without a real shortage.  count = 0
+ * disarms it.  AES_E_ARG if either is negative.  Process-wide. */
+int aes_test_fail_allocs(int skip, int count);
 
 /* Debug build only: exactly-once coverage of the batch kernel's work counter.
  * Each chunk (chunk_blocks consecutive blocks of one message, the unit a warp
@@ -399,6 +410,7 @@ typedef struct aes_srv_stats_t {
     double busy_s;          /* first arrival -> last completion            */
     int32_t worker_status;  /* AES_OK, or the first dispatcher CUDA error   */
     int32_t reserved;
+    uint64_t cancelled;     /* requests completed by aes_srv_cancel         */
 } aes_srv_stats_t;
 
 /* Create a server: key store for max_keys expanded schedules (device),
@@ -440,6 +452,25 @@ int aes_srv_results(aes_server *srv, int n, const uint64_t *tickets, int32_t *st
                     double *queue_s, int release);
 
 int aes_srv_stats(aes_server *srv, aes_srv_stats_t *out);
+
+/* Cancel a request that has not been launched yet (still queued: not arrived,
+ * or waiting for budget or a slot).  It completes at once with status
+ * AES_E_CANCELLED, its buffers are never touched, and aes_srv_drain no longer
+ * waits for it.  AES_E_BUSY if the request is already in a launched batch or
+ * done (it then completes, or has completed, normally); AES_E_NOTFOUND for an
+ * unknown or released ticket. */
+int aes_srv_cancel(aes_server *srv, uint64_t ticket);
+
+/* Registry of the device allocations requests may use.  While it is empty
+ * (the default) every buffer is accepted.  Once a range is registered,
+ * aes_srv_submit* accept a request only if its input and its output each lie
+ * entirely inside one registered range, and return AES_E_UNREGISTERED
+ * otherwise -- a host-side check before anything is launched, so that a
+ * descriptor can never point outside the caller's allocations.  Ranges may
+ * not overlap (AES_E_OVERLAP); unregistering (AES_E_NOTFOUND for an unknown
+ * base) affects later submissions only. */
+int aes_srv_register(aes_server *srv, const void *base_dev, size_t bytes);
+int aes_srv_unregister(aes_server *srv, const void *base_dev);
 
 /* Stop the dispatcher (requests not yet launched are dropped), wait for the
  * batches in flight and free everything. */

@@ -70,7 +70,8 @@ class aes_srv_stats_t(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("batches", ctypes.c_uint64),
                 ("bytes_completed", ctypes.c_uint64), ("inflight_bytes", ctypes.c_uint64),
                 ("peak_inflight_bytes", ctypes.c_uint64), ("pending", ctypes.c_uint64),
-                ("busy_s", ctypes.c_double), ("worker_status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("busy_s", ctypes.c_double), ("worker_status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("cancelled", ctypes.c_uint64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
@@ -138,6 +139,10 @@ _SIGNATURES = {
     "aes_srv_results": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _i]),
     "aes_srv_stats": (_i, [_vp, ctypes.POINTER(aes_srv_stats_t)]),
     "aes_srv_destroy": (_i, [_vp]),
+    "aes_srv_cancel": (_i, [_vp, ctypes.c_uint64]),
+    "aes_srv_register": (_i, [_vp, _vp, _sz]),
+    "aes_srv_unregister": (_i, [_vp, _vp]),
+    "aes_test_fail_allocs": (_i, [_i, _i]),
     "aes_device_table": (_i, [_i, _u32p]),
 }
 
@@ -400,6 +405,26 @@ def aes_srv_stats(srv: int) -> dict:
     s = aes_srv_stats_t()
     _check(lib().aes_srv_stats(_vp(srv), ctypes.byref(s)), "aes_srv_stats")
     return s.as_dict()
+
+
+def aes_srv_cancel(srv: int, ticket: int) -> None:
+    """Cancel a queued (not yet launched) request; raises AesError (AES_E_BUSY) once it is launched."""
+    _check(lib().aes_srv_cancel(_vp(srv), int(ticket)), "aes_srv_cancel")
+
+
+def aes_srv_register(srv: int, base_dev, nbytes: int) -> None:
+    """Add a device range to the server's registry of allowed request buffers."""
+    _check(lib().aes_srv_register(_vp(srv), _ptr(base_dev), int(nbytes)), "aes_srv_register")
+
+
+def aes_srv_unregister(srv: int, base_dev) -> None:
+    _check(lib().aes_srv_unregister(_vp(srv), _ptr(base_dev)), "aes_srv_unregister")
+
+
+def aes_test_fail_allocs(skip: int, count: int) -> None:
+    """Failure injection: of the library's own allocations from now on, the first
+    `skip` succeed and the next `count` fail as out of memory (count 0 disarms)."""
+    _check(lib().aes_test_fail_allocs(int(skip), int(count)), "aes_test_fail_allocs")
 
 
 def aes_srv_destroy(srv: int) -> None:

@@ -526,10 +526,8 @@ int lib_workspace(int dev, size_t need, void **ptr) {
             w.bytes = 0;
         }
         size_t sz = need < (1u << 20) ? (1u << 20) : need * 2;
-        if (cudaMalloc(&w.ptr, sz) != cudaSuccess) {
-            (void)cudaGetLastError();
-            return AES_E_NOMEM;
-        }
+        const int st = lib_malloc_device(&w.ptr, sz);
+        if (st != AES_OK) return st;
         w.bytes = sz;
     }
     *ptr = w.ptr;

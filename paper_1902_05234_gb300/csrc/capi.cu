@@ -171,6 +171,48 @@ int launch_ecb(int dir, const uint32_t *rk, int nr, const uint8_t *in, uint8_t *
     return launch_pdl(fn, grid, c.threads, smem, params, stream);
 }
 
+// ---------------------------------------------------------------------------
+// the library's own allocations, with a host-side failure injector
+// ---------------------------------------------------------------------------
+namespace {
+std::mutex g_inject_mu;
+int g_inject_skip = 0, g_inject_fail = 0;  // allocations to let through, then to fail
+
+// Whether this allocation is to fail (advancing the injector).
+bool take_injected_failure() {
+    std::lock_guard<std::mutex> lk(g_inject_mu);
+    if (g_inject_fail == 0) return false;
+    if (g_inject_skip > 0) {
+        --g_inject_skip;
+        return false;
+    }
+    --g_inject_fail;
+    return true;
+}
+}  // namespace
+
+int lib_malloc_device(void **p, size_t bytes) {
+    *p = nullptr;
+    if (take_injected_failure()) return AES_E_NOMEM;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        *p = nullptr;
+        return AES_E_NOMEM;
+    }
+    return AES_OK;
+}
+
+int lib_malloc_host(void **p, size_t bytes) {
+    *p = nullptr;
+    if (take_injected_failure()) return AES_E_NOMEM;
+    if (cudaMallocHost(p, bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        *p = nullptr;
+        return AES_E_NOMEM;
+    }
+    return AES_OK;
+}
+
 }  // namespace aesgb
 
 using namespace aesgb;
@@ -195,6 +237,8 @@ const char *aes_status_str(int status) {
     case AES_E_RANGE: return "AES_E_RANGE: size above the documented maximum";
     case AES_E_NOTFOUND: return "AES_E_NOTFOUND: unknown key id or ticket";
     case AES_E_CONFIG: return "AES_E_CONFIG: unsupported launch configuration";
+    case AES_E_CANCELLED: return "AES_E_CANCELLED: request cancelled before its launch";
+    case AES_E_UNREGISTERED: return "AES_E_UNREGISTERED: buffer outside every registered range";
     default: return "unknown status";
     }
 }
@@ -204,6 +248,14 @@ int aes_version(void) { return 10000; }
 int aes_wait_timeouts(unsigned long long *count) {
     if (!count) return AES_E_ARG;
     return read_wait_timeouts(count);
+}
+
+int aes_test_fail_allocs(int skip, int count) {
+    if (skip < 0 || count < 0) return AES_E_ARG;
+    std::lock_guard<std::mutex> lk(g_inject_mu);
+    g_inject_skip = count ? skip : 0;
+    g_inject_fail = count;
+    return AES_OK;
 }
 
 int aes_debug_bounds_violations(unsigned long long *count) {

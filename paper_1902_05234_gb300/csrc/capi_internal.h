@@ -17,6 +17,11 @@ int ensure_smem_attr(const void *fn, int dev, uint32_t bytes);
 // griddep_wait() before touching global memory).  AES_E_CUDA on failure.
 int launch_pdl(const void *fn, int grid, int threads, uint32_t smem, void **params, void *stream);
 int check_nrounds(int nr);
+// The library's own allocations (device memory, page-locked host memory),
+// through the failure injector of aes_test_fail_allocs.  AES_OK, or
+// AES_E_NOMEM with *p = nullptr.
+int lib_malloc_device(void **p, size_t bytes);
+int lib_malloc_host(void **p, size_t bytes);
 int check_buffers(const void *in, const void *out, size_t nblocks);
 void order_round_keys(int dir, const uint32_t *rk, int nr, RoundKeys *out);
 int validate_cfg(const aes_launch_cfg &c);

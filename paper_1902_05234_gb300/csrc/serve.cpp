@@ -18,10 +18,16 @@
 //     completion times are recorded and their bytes leave the budget.
 // Host waits are bounded (condition variables with timeouts); nothing on the
 // device waits.  Latency is host arrival -> host-observed completion.
+// Queued requests can be cancelled; an optional registry of device ranges
+// confines every request's buffers to the caller's allocations, checked on
+// the host at submission.  The dispatcher marks each batch's planning and
+// launch, and each retirement, as NVTX ranges (domain "aesgb") for nsys/ncu
+// timelines; with no tool attached they cost a few nanoseconds.
 #if defined(__linux__)
 #include <sys/prctl.h>
 #endif
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <atomic>
@@ -30,6 +36,8 @@
 #include <cstdint>
 #include <cstring>
 #include <deque>
+#include <iterator>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -86,11 +94,21 @@ struct Server {
     std::deque<Req> reqs;
     uint64_t base = 1;
     Req *find(uint64_t t) { return t >= base && t - base < reqs.size() ? &reqs[t - base] : nullptr; }
+    // registered device ranges, base -> bytes (disjoint); empty: no check
+    std::map<uintptr_t, size_t> regs;
+    // [p, p + n) inside one registered range
+    bool covered(const void *p, size_t n) const {
+        const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+        auto it = regs.upper_bound(a);
+        if (it == regs.begin()) return false;
+        --it;
+        return a - it->first <= it->second && n <= it->second - (a - it->first);
+    }
     std::thread worker;
     bool stop = false;
     int worker_error = AES_OK;
     // statistics
-    uint64_t n_submitted = 0, n_completed = 0, n_batches = 0, bytes_completed = 0;
+    uint64_t n_submitted = 0, n_completed = 0, n_batches = 0, bytes_completed = 0, n_cancelled = 0;
     double first_arrival = 0, last_done = 0;
 };
 
@@ -127,12 +145,33 @@ aes_batch_cfg serve_cfg(int sms, unsigned long long total_blocks) {
     return c;
 }
 
+nvtxDomainHandle_t nvtx_domain() {
+    static const nvtxDomainHandle_t d = nvtxDomainCreateA("aesgb");
+    return d;
+}
+
+// One NVTX range on the dispatcher thread for the lifetime of this object.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) {
+        nvtxEventAttributes_t a{};
+        a.version = NVTX_VERSION;
+        a.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+        a.messageType = NVTX_MESSAGE_TYPE_ASCII;
+        a.message.ascii = name;
+        nvtxDomainRangePushEx(nvtx_domain(), &a);
+    }
+    ~NvtxRange() { nvtxDomainRangePop(nvtx_domain()); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 // Retire finished slots (mu held).
 void retire_locked(Server *s) {
     for (Slot &sl : s->slots) {
         if (!sl.busy) continue;
         const cudaError_t q = cudaEventQuery(sl.ev);
         if (q == cudaErrorNotReady) continue;
+        const NvtxRange range("aes_srv retire");
         const double t = now_s();
         const bool ok = q == cudaSuccess;
         if (!ok) (void)cudaGetLastError();
@@ -192,6 +231,7 @@ bool dispatch_locked(Server *s, int sms) {
         ++n;
     }
     if (n == 0) return false;
+    const NvtxRange range("aes_srv plan+launch");
     // the plan (message order, chunk prefix, zeroed counters) is built here on
     // the host -- every request was validated at submission -- and uploaded
     // with the descriptors, so only the persistent kernel runs on the device
@@ -281,16 +321,21 @@ int aes_srv_create(size_t mem_budget_bytes, int max_keys, int max_batch, int slo
     s->key_nr.assign(static_cast<size_t>(max_keys), -1);
     int st = current_device(&s->dev);
     const size_t rk_bytes = static_cast<size_t>(max_keys) * kRkStrideWords * 4;
-    bool ok = st == AES_OK && cudaMalloc(&s->d_rk_enc, rk_bytes) == cudaSuccess &&
-              cudaMalloc(&s->d_rk_dec, rk_bytes) == cudaSuccess;
+    void *rk_enc = nullptr, *rk_dec = nullptr;
+    bool ok = st == AES_OK && (st = lib_malloc_device(&rk_enc, rk_bytes)) == AES_OK &&
+              (st = lib_malloc_device(&rk_dec, rk_bytes)) == AES_OK;
+    s->d_rk_enc = static_cast<uint32_t *>(rk_enc);
+    s->d_rk_dec = static_cast<uint32_t *>(rk_dec);
     s->slots.resize(static_cast<size_t>(slots));
     for (Slot &sl : s->slots) {
         if (!ok) break;
         sl.buf_bytes = plan_offset(max_batch) + aes_batch_workspace_bytes(max_batch);
         void *hb = nullptr, *db = nullptr;
         ok = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) == cudaSuccess &&
-             cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) == cudaSuccess &&
-             cudaMallocHost(&hb, sl.buf_bytes) == cudaSuccess && cudaMalloc(&db, sl.buf_bytes) == cudaSuccess;
+             cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) st = AES_E_CUDA;
+        ok = ok && (st = lib_malloc_host(&hb, sl.buf_bytes)) == AES_OK &&
+             (st = lib_malloc_device(&db, sl.buf_bytes)) == AES_OK;
         sl.h_desc = static_cast<aes_desc *>(hb);
         sl.d_desc = static_cast<aes_desc *>(db);
         sl.tickets.reserve(static_cast<size_t>(max_batch));
@@ -298,7 +343,7 @@ int aes_srv_create(size_t mem_budget_bytes, int max_keys, int max_batch, int slo
     if (!ok) {
         (void)cudaGetLastError();
         free_server(s);
-        return st == AES_OK ? AES_E_NOMEM : st;
+        return st == AES_OK ? AES_E_CUDA : st;
     }
     s->worker = std::thread(worker_main, s);
     *out = reinterpret_cast<aes_server *>(s);
@@ -334,6 +379,8 @@ static int submit_locked(Server *s, int key_id, int dir, const uint8_t *in, uint
     const int st = check_buffers(in ? in : reinterpret_cast<const uint8_t *>(16),
                                  out ? out : reinterpret_cast<uint8_t *>(16), nbytes / 16);
     if (nbytes && st != AES_OK) return st;
+    if (nbytes && !s->regs.empty() && !(s->covered(in, nbytes) && s->covered(out, nbytes)))
+        return AES_E_UNREGISTERED;
     const uint64_t t = s->base + s->reqs.size();
     Req r;
     r.key_id = key_id;
@@ -458,6 +505,54 @@ int aes_srv_results(aes_server *h, int n, const uint64_t *tickets, int32_t *stat
     return missing == 0 ? AES_OK : AES_E_BUSY;
 }
 
+int aes_srv_cancel(aes_server *h, uint64_t ticket) {
+    Server *s = as_server(h);
+    if (!s) return AES_E_ARG;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        Req *r = s->find(ticket);
+        if (!r || r->released) return AES_E_NOTFOUND;
+        // queued requests are exactly those still in `pending`: the
+        // dispatcher removes a request from it when it packs it into a batch
+        const auto it = std::find(s->pending.begin(), s->pending.end(), ticket);
+        if (r->done || it == s->pending.end()) return AES_E_BUSY;
+        s->pending.erase(it);
+        r->done = true;
+        r->done_t = now_s();
+        r->admitted = r->done_t;
+        r->status = AES_E_CANCELLED;
+        s->n_completed++;
+        s->n_cancelled++;
+    }
+    s->cv_done.notify_all();
+    s->cv_work.notify_one();  // the requests behind it may fit now
+    return AES_OK;
+}
+
+int aes_srv_register(aes_server *h, const void *base_dev, size_t bytes) {
+    Server *s = as_server(h);
+    if (!s || !base_dev || bytes == 0) return AES_E_ARG;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(base_dev);
+    if (bytes > UINTPTR_MAX - a) return AES_E_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    // disjoint from its neighbours on both sides
+    auto next = s->regs.lower_bound(a);
+    if (next != s->regs.end() && next->first - a < bytes) return AES_E_OVERLAP;
+    if (next != s->regs.begin()) {
+        auto prev = std::prev(next);
+        if (a - prev->first < prev->second) return AES_E_OVERLAP;
+    }
+    s->regs.emplace(a, bytes);
+    return AES_OK;
+}
+
+int aes_srv_unregister(aes_server *h, const void *base_dev) {
+    Server *s = as_server(h);
+    if (!s || !base_dev) return AES_E_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    return s->regs.erase(reinterpret_cast<uintptr_t>(base_dev)) ? AES_OK : AES_E_NOTFOUND;
+}
+
 int aes_srv_stats(aes_server *h, aes_srv_stats_t *out) {
     Server *s = as_server(h);
     if (!s || !out) return AES_E_ARG;
@@ -471,6 +566,8 @@ int aes_srv_stats(aes_server *h, aes_srv_stats_t *out) {
     out->pending = s->pending.size();
     out->busy_s = s->last_done > s->first_arrival ? s->last_done - s->first_arrival : 0.0;
     out->worker_status = s->worker_error;
+    out->reserved = 0;
+    out->cancelled = s->n_cancelled;
     return AES_OK;
 }
 

@@ -23,7 +23,7 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_status_strings(lib):
-    for st in range(0, -13, -1):
+    for st in range(0, -15, -1):
         s = aesgb.aes_status_str(st)
         assert s and s != "unknown status"
     assert aesgb.aes_status_str(5) == "unknown status"
@@ -96,6 +96,21 @@ def test_debug_counter_is_debug_build_only(lib):
     c = [ctypes.c_ulonglong(7) for _ in range(3)]
     assert lib.aes_debug_batch_coverage(*[ctypes.byref(x) for x in c]) == -12
     assert [x.value for x in c] == [0, 0, 0]
+
+
+def test_fail_allocs_hook_arguments(lib):
+    """The allocation-failure injector is host state only: setting and
+    clearing it needs no device; a negative count is an argument error."""
+    assert lib.aes_test_fail_allocs(-1, 1) == -1
+    assert lib.aes_test_fail_allocs(0, -1) == -1
+    assert lib.aes_test_fail_allocs(2, 3) == 0
+    assert lib.aes_test_fail_allocs(0, 0) == 0
+
+
+def test_server_calls_reject_null_handle(lib):
+    assert lib.aes_srv_cancel(None, 1) == -1
+    assert lib.aes_srv_register(None, 1 << 20, 4096) == -1
+    assert lib.aes_srv_unregister(None, 1 << 20) == -1
 
 
 def test_default_cfg_is_valid():

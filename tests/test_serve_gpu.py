@@ -141,3 +141,139 @@ def test_errors_and_bounded_wait(server):
         assert not done
     finally:
         aesgb.aes_srv_destroy(srv2)                             # drops the future request
+
+
+def test_cancel_queued_requests(orc):
+    """Requests still queued (arrival 30 s ahead) are cancelled: they complete
+    at once with AES_E_CANCELLED, drain stops waiting for them and their
+    outputs are never written.  A request already done cannot be cancelled;
+    the ones behind a cancelled request still run and are exact."""
+    torch = torch_cuda()
+    srv = aesgb.aes_srv_create(8 << 20, max_keys=1, max_batch=16, slots=2)
+    try:
+        key = wl.random_key(256, 400).tobytes()
+        aesgb.aes_srv_put_key(srv, 0, 256, key)
+        sizes = [4096] * 6
+        a = Arena(torch, sizes, 401)
+        arrivals = [30.0, 0.0, 30.0, 0.0, 30.0, 0.0]
+        st, t = aesgb.aes_srv_submit_many(srv, [0] * 6, [0, 1, 0, 1, 0, 1], a.ins(), a.outs(), sizes, arrivals)
+        assert st == 0
+        for i in (0, 2, 4):
+            aesgb.aes_srv_cancel(srv, int(t[i]))
+        aesgb.aes_srv_drain(srv, 10000)                          # returns: nothing left to wait for
+        status, _, _ = aesgb.aes_srv_results(srv, t)
+        assert list(status) == [-13, 0, -13, 0, -13, 0]
+        out = a.out.cpu().numpy()
+        for i in (0, 2, 4):
+            assert np.all(a.msg(out, i) == 0x5A), i
+        for i in (1, 3, 5):
+            assert np.array_equal(a.msg(out, i), orc.ecb(1, key, a.msg(a.data, i), nthreads=1)), i
+        with pytest.raises(aesgb.AesError) as e:
+            aesgb.aes_srv_cancel(srv, int(t[1]))                # done already
+        assert e.value.status == -9
+        with pytest.raises(aesgb.AesError) as e:
+            aesgb.aes_srv_cancel(srv, 10 ** 9)                  # never issued
+        assert e.value.status == -11
+        stats = aesgb.aes_srv_stats(srv)
+        assert stats["cancelled"] == 3 and stats["completed"] == 6 and stats["bytes_completed"] == 3 * 4096
+    finally:
+        aesgb.aes_srv_destroy(srv)
+
+
+def test_registered_ranges_confine_buffers(orc):
+    """With a registry, a request is accepted only if its input and output
+    each lie inside one registered range (checked on the host before any
+    launch); overlapping registrations are refused; an empty registry accepts
+    every buffer again."""
+    torch = torch_cuda()
+    srv = aesgb.aes_srv_create(8 << 20, max_keys=1, max_batch=16, slots=1)
+    try:
+        key = wl.random_key(128, 402).tobytes()
+        aesgb.aes_srv_put_key(srv, 0, 128, key)
+        data = wl.random_bytes(1 << 16, 403)
+        n = data.size
+        # each registered range is the first half of a larger allocation, so
+        # that a request running past it stays inside memory it may touch
+        src_all = torch.zeros(2 * n, dtype=torch.uint8, device="cuda")
+        dst_all = torch.full((2 * n,), 0x5A, dtype=torch.uint8, device="cuda")
+        src, dst = src_all[:n], dst_all[:n]
+        src.copy_(torch.from_numpy(data))
+        other = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        aesgb.aes_srv_register(srv, src, n)
+        aesgb.aes_srv_register(srv, dst, n)
+        for base, size in ((src.data_ptr() + 256, 256), (dst.data_ptr() - 256, 512)):
+            with pytest.raises(aesgb.AesError) as e:
+                aesgb.aes_srv_register(srv, base, size)          # overlaps a registered range
+            assert e.value.status == -5
+        refused = [(other.data_ptr(), dst.data_ptr(), 4096),           # input unregistered
+                   (src.data_ptr(), other.data_ptr(), 4096),           # output unregistered
+                   (src.data_ptr() + n - 4096, dst.data_ptr(), 8192),  # input runs past its range
+                   (src.data_ptr(), dst.data_ptr() + 16, n)]           # output runs past its range
+        for ip, op, nb in refused:
+            with pytest.raises(aesgb.AesError) as e:
+                aesgb.aes_srv_submit(srv, 0, 0, ip, op, nb)
+            assert e.value.status == -14, (ip - src.data_ptr(), op - dst.data_ptr(), nb)
+        t = aesgb.aes_srv_submit(srv, 0, 0, src, dst, n)          # whole ranges: accepted
+        s, _ = aesgb.aes_srv_wait(srv, t, 10000)
+        assert s == 0
+        assert np.array_equal(dst.cpu().numpy(), orc.ecb(0, key, data, nthreads=4))
+        aesgb.aes_srv_unregister(srv, src)
+        with pytest.raises(aesgb.AesError) as e:
+            aesgb.aes_srv_unregister(srv, src)
+        assert e.value.status == -11
+        aesgb.aes_srv_unregister(srv, dst)
+        t = aesgb.aes_srv_submit(srv, 0, 1, dst, other, n)        # registry empty: any buffer
+        s, _ = aesgb.aes_srv_wait(srv, t, 10000)
+        assert s == 0 and torch.equal(other, src)
+        stats = aesgb.aes_srv_stats(srv)
+        assert stats["submitted"] == 2 and stats["worker_status"] == 0
+    finally:
+        aesgb.aes_srv_destroy(srv)
+
+
+def test_injected_allocation_failures(orc):
+    """Host-side failure injection.  aes_srv_create makes six allocations
+    (two key stores, then a page-locked and a device buffer per slot); with
+    the k-th of them failing it returns AES_E_NOMEM, frees what it had, and
+    the library stays usable.  The library-owned batch workspace, grown for a
+    batch larger than any before, reports the same and allocates on the next
+    call."""
+    torch = torch_cuda()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    try:
+        for k in range(6):
+            aesgb.aes_test_fail_allocs(k, 1)
+            with pytest.raises(aesgb.AesError) as e:
+                aesgb.aes_srv_create(1 << 20, max_keys=4, max_batch=8, slots=2)
+            assert e.value.status == -7, k
+        aesgb.aes_test_fail_allocs(0, 0)
+        srv = aesgb.aes_srv_create(1 << 20, max_keys=4, max_batch=8, slots=2)
+        aesgb.aes_srv_destroy(srv)
+        # 200,000 one-block messages of one key: a 4 MB plan, above the
+        # 1 MiB workspace the library keeps after small batches
+        n = 200_000
+        key = wl.random_key(128, 405).tobytes()
+        enc, _, nr = aesgb.aes_expand_key(128, key)
+        data = wl.random_bytes(16 * n, 406)
+        x = torch.from_numpy(data).cuda()
+        y = torch.full_like(x, 0x5A)
+        rk = torch.from_numpy(enc.view(np.uint8).copy()).cuda()
+        off = 16 * np.arange(n, dtype=np.uint64)
+        table = aesgb.pack_descs(np.full(n, rk.data_ptr(), np.uint64), x.data_ptr() + off, y.data_ptr() + off,
+                                 np.ones(n), np.full(n, nr), np.zeros(n))
+        desc = torch.from_numpy(table.view(np.uint8).copy()).cuda()
+        aesgb.aes_test_fail_allocs(0, 1)
+        with pytest.raises(aesgb.AesError) as e:
+            aesgb.aes_ecb_batch(desc, n)
+        assert e.value.status == -7
+        torch.cuda.synchronize()
+        assert bool((y == 0x5A).all())                              # nothing launched
+        aesgb.aes_ecb_batch(desc, n)                                # the next call allocates and runs
+        torch.cuda.synchronize()
+        assert np.array_equal(y.cpu().numpy(), orc.ecb(0, key, data, nthreads=4))
+    finally:
+        aesgb.aes_test_fail_allocs(0, 0)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] > free0 - (64 << 20)       # nothing large leaked
+
