@@ -44,7 +44,8 @@ MIB = 1 << 20
 METRIC = "AES-128 ECB enc/dec throughput (single 1 GiB buffer, HBM-resident)"
 UNIT = "Gbit/s"
 KERNEL_SOURCES = ["paper_1902_05234_gb300/csrc/aes_kernels.cuh",
-                  "paper_1902_05234_gb300/csrc/aes_tables.h"]
+                  "paper_1902_05234_gb300/csrc/aes_tables.h",
+                  "paper_1902_05234_gb300/csrc/bounds.cuh"]
 
 
 def parse_args():
