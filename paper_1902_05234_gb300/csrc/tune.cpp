@@ -1,13 +1,16 @@
 // tune.cpp -- launch-configuration choice: size-adaptive defaults and an
 // autotuner that times candidate configurations on the caller's buffers.
 //
-// The single-buffer kernels are tuned per (SM count, direction, Nr, size
-// class), size class = floor(log4(nblocks)); the batch kernel per SM count.
-// Tuned entries live in memory and, when AESGB_TUNE_CACHE names a file, are
-// loaded from it on first use and written back after every tuning run.  The
-// file is plain text, one entry per line:
-//   ecb   <sms> <dir> <nr> <class> <threads> <blocks_per_thread> <layout> <ctas_per_sm>
-//   batch <sms> <threads> <blocks_per_thread> <chunk_passes> <ctas_per_sm>
+// The single-buffer kernels are tuned per (device, direction, Nr, size
+// class), size class = floor(log4(nblocks)); the batch kernel per device.  A
+// device is its model tag (32-bit FNV-1a hash of the device name and compute
+// capability) and its SM count, so a cache written on one GPU model is not
+// applied to another.  Tuned entries live in memory and, when
+// AESGB_TUNE_CACHE names a file, are loaded from it on first use and written
+// back after every tuning run.  The file is plain text, one entry per line
+// (lines of another format are ignored):
+//   ecb   <tag hex> <sms> <dir> <nr> <class> <threads> <blocks_per_thread> <layout> <ctas_per_sm>
+//   batch <tag hex> <sms> <threads> <blocks_per_thread> <chunk_passes> <ctas_per_sm>
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -25,10 +28,11 @@
 namespace aesgb {
 namespace {
 
-using EcbKey = std::tuple<int, int, int, int>;  // sms, dir, nr, class
+using DevKey = std::pair<uint32_t, int>;                   // model tag, sms
+using EcbKey = std::tuple<uint32_t, int, int, int, int>;  // tag, sms, dir, nr, class
 std::mutex g_mu;
 std::map<EcbKey, aes_launch_cfg> g_ecb;
-std::map<int, aes_batch_cfg> g_batch;  // sms -> cfg
+std::map<DevKey, aes_batch_cfg> g_batch;
 bool g_env_loaded = false;
 
 int size_class(size_t nblocks) {
@@ -47,19 +51,60 @@ int current_sms() {
     return s > 0 ? s : 0;
 }
 
+// FNV-1a over the device name and compute capability; 0 without a device.
+uint32_t model_tag(int dev) {
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    uint32_t h = 2166136261u;
+    auto mix = [&h](unsigned char c) { h = (h ^ c) * 16777619u; };
+    for (const char *c = p.name; *c; ++c) mix(static_cast<unsigned char>(*c));
+    mix(static_cast<unsigned char>(p.major));
+    mix(static_cast<unsigned char>(p.minor));
+    return h;
+}
+
+// (model tag, SM count) of the current device, the tag looked up once per device.
+DevKey current_devkey() {
+    constexpr int kMaxDev = 64;
+    static std::mutex mu;
+    static uint32_t tags[kMaxDev];
+    static bool known[kMaxDev];
+    int dev = 0;
+    if (current_device(&dev) != AES_OK || dev < 0 || dev >= kMaxDev) return DevKey{0u, 0};
+    uint32_t tag;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!known[dev]) {
+            tags[dev] = model_tag(dev);
+            known[dev] = true;
+        }
+        tag = tags[dev];
+    }
+    return DevKey{tag, current_sms()};
+}
+
+EcbKey ecb_key(int dir, int nrounds, size_t nblocks) {
+    const DevKey d = current_devkey();
+    return EcbKey{d.first, d.second, dir, nrounds, size_class(nblocks)};
+}
+
 int load_file_locked(const char *path) {
     FILE *f = std::fopen(path, "r");
     if (!f) return AES_E_ARG;
     char line[256];
     while (std::fgets(line, sizeof line, f)) {
+        unsigned int tag = 0;
         int a[8];
-        if (std::sscanf(line, "ecb %d %d %d %d %d %d %d %d", &a[0], &a[1], &a[2], &a[3], &a[4], &a[5], &a[6],
-                        &a[7]) == 8) {
+        if (std::sscanf(line, "ecb %x %d %d %d %d %d %d %d %d", &tag, &a[0], &a[1], &a[2], &a[3], &a[4], &a[5],
+                        &a[6], &a[7]) == 9) {
             aes_launch_cfg c{a[4], a[5], a[6], a[7]};
-            if (validate_cfg(c) == AES_OK) g_ecb[EcbKey{a[0], a[1], a[2], a[3]}] = c;
-        } else if (std::sscanf(line, "batch %d %d %d %d %d", &a[0], &a[1], &a[2], &a[3], &a[4]) == 5) {
+            if (validate_cfg(c) == AES_OK) g_ecb[EcbKey{tag, a[0], a[1], a[2], a[3]}] = c;
+        } else if (std::sscanf(line, "batch %x %d %d %d %d %d", &tag, &a[0], &a[1], &a[2], &a[3], &a[4]) == 6) {
             aes_batch_cfg c{a[1], a[2], a[3], a[4]};
-            if (validate_batch_cfg(c) == AES_OK) g_batch[a[0]] = c;
+            if (validate_batch_cfg(c) == AES_OK) g_batch[DevKey{tag, a[0]}] = c;
         }
     }
     std::fclose(f);
@@ -69,16 +114,17 @@ int load_file_locked(const char *path) {
 int save_file_locked(const char *path) {
     FILE *f = std::fopen(path, "w");
     if (!f) return AES_E_ARG;
-    std::fprintf(f, "# aesgb tune cache v1\n");
+    std::fprintf(f, "# aesgb tune cache v2\n");
     for (const auto &kv : g_ecb) {
         const auto &k = kv.first;
         const auto &c = kv.second;
-        std::fprintf(f, "ecb %d %d %d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k),
-                     std::get<3>(k), c.threads, c.blocks_per_thread, c.layout, c.ctas_per_sm);
+        std::fprintf(f, "ecb %08x %d %d %d %d %d %d %d %d\n", static_cast<unsigned int>(std::get<0>(k)),
+                     std::get<1>(k), std::get<2>(k), std::get<3>(k), std::get<4>(k), c.threads, c.blocks_per_thread,
+                     c.layout, c.ctas_per_sm);
     }
     for (const auto &kv : g_batch)
-        std::fprintf(f, "batch %d %d %d %d %d\n", kv.first, kv.second.threads, kv.second.blocks_per_thread,
-                     kv.second.chunk_passes, kv.second.ctas_per_sm);
+        std::fprintf(f, "batch %08x %d %d %d %d %d\n", static_cast<unsigned int>(kv.first.first), kv.first.second,
+                     kv.second.threads, kv.second.blocks_per_thread, kv.second.chunk_passes, kv.second.ctas_per_sm);
     const bool ok = std::fclose(f) == 0;
     return ok ? AES_OK : AES_E_ARG;
 }
@@ -139,12 +185,12 @@ aes_launch_cfg default_cfg(int /*dir*/, int /*nrounds*/, size_t nblocks) {
 }
 
 aes_launch_cfg tuned_or_default_cfg(int dir, int nrounds, size_t nblocks) {
-    const int sms = current_sms();
+    const EcbKey key = ecb_key(dir, nrounds, nblocks);
     {
         std::lock_guard<std::mutex> lk(g_mu);
         load_env_locked();
         if (!g_ecb.empty()) {
-            auto it = g_ecb.find(EcbKey{sms, dir, nrounds, size_class(nblocks)});
+            auto it = g_ecb.find(key);
             if (it != g_ecb.end()) return it->second;
         }
     }
@@ -161,10 +207,10 @@ aes_batch_cfg default_batch_cfg() {
 }
 
 aes_batch_cfg batch_cfg_for(int /*n*/) {
-    const int sms = current_sms();
+    const DevKey key = current_devkey();
     std::lock_guard<std::mutex> lk(g_mu);
     load_env_locked();
-    auto it = g_batch.find(sms);
+    auto it = g_batch.find(key);
     return it != g_batch.end() ? it->second : default_batch_cfg();
 }
 
@@ -209,7 +255,7 @@ int aes_tune_ecb(int dir, int nrounds, const uint32_t *rk, const uint8_t *in, ui
     {
         std::lock_guard<std::mutex> lk(g_mu);
         load_env_locked();
-        g_ecb[EcbKey{current_sms(), dir, nrounds, size_class(nblocks)}] = best_cfg;
+        g_ecb[ecb_key(dir, nrounds, nblocks)] = best_cfg;
         save_env_locked();
     }
     if (best) *best = best_cfg;
@@ -239,7 +285,7 @@ int aes_tune_batch(const aes_desc *desc_dev, int n, void *ws, size_t ws_bytes, v
     {
         std::lock_guard<std::mutex> lk(g_mu);
         load_env_locked();
-        g_batch[current_sms()] = best_cfg;
+        g_batch[current_devkey()] = best_cfg;
         save_env_locked();
     }
     if (best) *best = best_cfg;
@@ -275,7 +321,7 @@ int aes_tune_set_ecb(int dir, int nrounds, size_t nblocks, const aes_launch_cfg 
     if (st != AES_OK) return st;
     std::lock_guard<std::mutex> lk(g_mu);
     load_env_locked();
-    g_ecb[EcbKey{current_sms(), dir, nrounds, size_class(nblocks)}] = *cfg;
+    g_ecb[ecb_key(dir, nrounds, nblocks)] = *cfg;
     return AES_OK;
 }
 

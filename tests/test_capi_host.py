@@ -113,6 +113,31 @@ def test_server_calls_reject_null_handle(lib):
     assert lib.aes_srv_unregister(None, 1 << 20) == -1
 
 
+def test_tune_cache_entries_of_another_device_model_are_not_applied(tmp_path):
+    """Cache lines carry the device's model tag: an entry written for another
+    model (tag deadbeef) or in the untagged older format is not used."""
+    aesgb.aes_tune_clear()
+    try:
+        c = aesgb.make_cfg(threads=256, blocks_per_thread=4, layout=aesgb.LAYOUT_R1, ctas_per_sm=0)
+        aesgb.aes_tune_set_ecb(1, 12, 1 << 22, c)
+        path = tmp_path / "tune.txt"
+        aesgb.aes_tune_save(str(path))
+        mine = [ln for ln in path.read_text().splitlines() if ln.startswith("ecb ")]
+        assert len(mine) == 1
+        fields = mine[0].split()
+        other = " ".join(["ecb", "deadbeef"] + fields[2:])
+        untagged = " ".join(["ecb"] + fields[2:])
+        path.write_text("# aesgb tune cache v2\n" + other + "\n" + untagged + "\n")
+        aesgb.aes_tune_clear()
+        aesgb.aes_tune_load(str(path))
+        assert aesgb.aes_ecb_get_cfg(1, 12, 1 << 22).layout == aesgb.LAYOUT_R4   # the default
+        path.write_text("# aesgb tune cache v2\n" + mine[0] + "\n")
+        aesgb.aes_tune_load(str(path))
+        assert aesgb.aes_ecb_get_cfg(1, 12, 1 << 22).as_dict() == c.as_dict()
+    finally:
+        aesgb.aes_tune_clear()
+
+
 def test_default_cfg_is_valid():
     for d in (0, 1):
         for nr in (10, 12, 14):
