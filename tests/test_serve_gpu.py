@@ -277,3 +277,54 @@ def test_injected_allocation_failures(orc):
     torch.cuda.synchronize()
     assert torch.cuda.mem_get_info()[0] > free0 - (64 << 20)       # nothing large leaked
 
+
+
+def test_cancel_races_dispatch_under_load(orc):
+    """Cancellation racing the dispatcher: 1,500 requests arrive over about
+    30 ms while every third one is cancelled right after submission.  Each
+    request ends exactly one way: cancelled (AES_E_CANCELLED, output never
+    written) or completed bit-exact; the counts add up."""
+    torch = torch_cuda()
+    srv = aesgb.aes_srv_create(64 << 20, max_keys=4, max_batch=64, slots=3)
+    try:
+        keys = {}
+        g = wl.rng(410)
+        for k in range(4):
+            kb = (128, 192, 256, 128)[k]
+            keys[k] = g.integers(0, 256, kb // 8, dtype=np.uint8).tobytes()
+            aesgb.aes_srv_put_key(srv, k, kb, keys[k])
+        n = 1500
+        sizes = wl.log_uniform_lengths(n, 16, 64 * 1024, g)
+        key_ids = g.integers(0, 4, n)
+        dirs = g.integers(0, 2, n)
+        arrivals = np.sort(g.uniform(0.0, 0.03, n))
+        a = Arena(torch, sizes, 411)
+        st, t = aesgb.aes_srv_submit_many(srv, key_ids, dirs, a.ins(), a.outs(), sizes, arrivals)
+        assert st == 0
+        outcome = {}
+        for i in range(0, n, 3):
+            try:
+                aesgb.aes_srv_cancel(srv, int(t[i]))
+                outcome[i] = "cancelled"
+            except aesgb.AesError as e:
+                assert e.status == -9, e.status                      # already launched
+                outcome[i] = "launched"
+        aesgb.aes_srv_drain(srv, 60000)
+        status, _, _ = aesgb.aes_srv_results(srv, t)
+        out = a.out.cpu().numpy()
+        n_cancelled = 0
+        for i in range(n):
+            if status[i] == -13:
+                assert outcome.get(i) == "cancelled", i
+                assert np.all(a.msg(out, i) == 0x5A), i
+                n_cancelled += 1
+            else:
+                assert status[i] == 0 and outcome.get(i) != "cancelled", (i, status[i])
+                exp = orc.ecb(int(dirs[i]), keys[int(key_ids[i])], a.msg(a.data, i), nthreads=1)
+                assert np.array_equal(a.msg(out, i), exp), i
+        stats = aesgb.aes_srv_stats(srv)
+        assert stats["cancelled"] == n_cancelled and stats["completed"] == n
+        assert stats["bytes_completed"] == int(sizes[status == 0].sum())
+        assert 0 < n_cancelled                                            # the race was exercised
+    finally:
+        aesgb.aes_srv_destroy(srv)
