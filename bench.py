@@ -49,29 +49,32 @@ KERNEL_SOURCES = ["paper_1902_05234_gb300/csrc/aes_kernels.cuh",
 
 
 def parse_args():
-    p = argparse.ArgumentParser()
-    p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=200)
-    p.add_argument("--warmup", type=int, default=5)
-    p.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    p = argparse.ArgumentParser(
+        description="Bulk AES ECB on one or more GB300s: one JSON line with the timed throughput, its roofline, "
+                    "the end-to-end figure, the other sections and the CPU oracle baseline.")
+    p.add_argument("--gpus", type=int, default=1, help="GPUs (one process each under torchrun; replicas)")
+    p.add_argument("--steps", type=int, default=200, help="timed steps (one encrypt + one decrypt launch each)")
+    p.add_argument("--warmup", type=int, default=5, help="untimed warm-up steps before the timed ones")
+    p.add_argument("--impl", choices=["gb300", "reference"], default="gb300",
+                   help="gb300: the CUDA kernels; reference: the CPU oracle on this host's cores")
     p.add_argument("--bytes", type=int, default=GIB, help="buffer size per rank")
-    p.add_argument("--keybits", type=int, default=128)
-    p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--no-sweep", action="store_true")
-    p.add_argument("--no-batched", action="store_true")
-    p.add_argument("--no-served", action="store_true")
-    p.add_argument("--no-tune", action="store_true")
-    p.add_argument("--no-stress", action="store_true")
+    p.add_argument("--keybits", type=int, default=128, help="AES key size of the timed workload (128, 192, 256)")
+    p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer (end-to-end) measurement")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--no-sweep", action="store_true", help="skip the size x key size x direction sweep")
+    p.add_argument("--no-batched", action="store_true", help="skip the batched (descriptor table) section")
+    p.add_argument("--no-served", action="store_true", help="skip the continuous-batching server section")
+    p.add_argument("--no-tune", action="store_true", help="time the default launch configurations, no autotuning")
+    p.add_argument("--no-stress", action="store_true", help="skip the 16 GiB in-place AES-256 decryption")
     p.add_argument("--no-ct", action="store_true", help="skip the constant-time (bitsliced) kernel")
-    p.add_argument("--served-requests", type=int, default=20000)
+    p.add_argument("--served-requests", type=int, default=20000, help="requests per load point of the served sweep")
     p.add_argument("--served-slots", type=int, default=4, help="in-flight batch slots of the served section's server")
     p.add_argument("--batch-n", type=int, default=4096, help="messages in the batched workload")
     p.add_argument("--batch-max-bytes", type=int, default=16 * MIB, help="largest message of the batched workload")
     p.add_argument("--study", action="store_true",
                    help="placement / granularity study (the paper's section 4 design axis) instead of the bench")
-    p.add_argument("--study-reps", type=int, default=5)
-    p.add_argument("--study-warmup", type=int, default=2)
+    p.add_argument("--study-reps", type=int, default=5, help="timed repetitions per study variant")
+    p.add_argument("--study-warmup", type=int, default=2, help="warm-up repetitions per study variant")
     return p.parse_args()
 
 
