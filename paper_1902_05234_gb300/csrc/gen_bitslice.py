@@ -41,7 +41,7 @@ every lambda of trace 1 and every isomorphism and keeps the cheapest.
 
 Usage:  python gen_bitslice.py            # writes bitslice_circuits.h
         python gen_bitslice.py --check    # exit 1 if the header is stale
-        python gen_bitslice.py --search   # print the cost of every tower (about an hour)
+        python gen_bitslice.py --search   # print the cost of every tower (minutes, on all cores)
 """
 import argparse
 import itertools
@@ -400,6 +400,14 @@ def _lut_for(T, a, b, c, full=0xFFFF):
 
 
 _INV_PLANS = {}
+_INV_MAX_COMBOS = 4_000_000
+
+
+def _prod(xs):
+    r = 1
+    for x in xs:
+        r *= x
+    return r
 
 
 def inverse_plan(mod):
@@ -441,6 +449,13 @@ def inverse_plan(mod):
                         pair[k].append((g1, g2, i, lut))
                         break
     options = [[("s",) + o for o in single[k]] if single[k] else [("p",) + o for o in pair[k]] for k in range(4)]
+    # The choice below is exhaustive up to _INV_MAX_COMBOS combinations (the
+    # default tower's modulus needs about 3.2 million).  Beyond that the
+    # longest option lists keep only their first halves, repeatedly, and the
+    # plan is the best of what is left: an upper bound, not the optimum.
+    while _prod(len(o) for o in options) > _INV_MAX_COMBOS:
+        k = max(range(4), key=lambda i: len(options[i]))
+        options[k] = options[k][:max(1, len(options[k]) // 2)]
     best = None
     for combo in itertools.product(*options):
         used = set()
@@ -710,20 +725,27 @@ def emit(circuits, towers, params, outs):
     return "\n".join(lines)
 
 
+def _search_one(p):
+    circ, _, _ = build_all((p, p), restarts=4)
+    e = len(circ["sbox_enc"].gates)
+    dcost = len(circ["sbox_core_dec"].gates) * 4 + len(circ["inv_mix_out"].gates)
+    return p, e, dcost
+
+
 def search():
+    """Cost of every tower, on all host cores: the encryption S-box's gates,
+    and a decryption column's (four inverse S-box cores and the InvMixColumns
+    output circuit)."""
+    import multiprocessing
+    params = [(mod, lam, bi, side)
+              for mod in QUARTICS for lam in range(1, 16) if g16_trace(lam, mod) == 1
+              for bi in range(Tower(mod, lam, 0).nroots) for side in (0, 1)]
     results = {"enc": [], "dec": []}
-    for mod in QUARTICS:
-        for lam in range(1, 16):
-            if g16_trace(lam, mod) != 1:
-                continue
-            for bi in range(Tower(mod, lam, 0).nroots):
-                for side in (0, 1):
-                    p = (mod, lam, bi, side)
-                    circ, _, _ = build_all((p, p), restarts=4)
-                    e = len(circ["sbox_enc"].gates)
-                    dcost = len(circ["sbox_core_dec"].gates) * 4 + len(circ["inv_mix_out"].gates)
-                    results["enc"].append((e, p))
-                    results["dec"].append((dcost, p))
+    with multiprocessing.Pool() as pool:
+        for n, (p, e, dcost) in enumerate(pool.imap_unordered(_search_one, params), 1):
+            print(f"[{n}/{len(params)}] tower {p}: encryption S-box {e}, decryption column {dcost}", flush=True)
+            results["enc"].append((e, p))
+            results["dec"].append((dcost, p))
     for k in results:
         results[k].sort()
         print(k, results[k][:8])
