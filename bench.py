@@ -676,6 +676,9 @@ STUDY_VARIANTS = [  # (label, layout, blocks/thread, threads)
     ("shared, 4 replicated tables, 64 B/thread", 0, 4, 512),
     ("shared, 4 replicated tables, TMA-staged input, 32 B/thread", 4, 2, 1024),
     ("shared, 4 replicated tables, TMA-staged input, 64 B/thread", 4, 4, 512),
+    ("shared, 2 replicated tables + one rotation per column, 16 B/thread", 5, 1, 1024),
+    ("shared, 2 replicated tables + one rotation per column, 32 B/thread", 5, 2, 1024),
+    ("shared, 2 replicated tables + one rotation per column, 64 B/thread", 5, 4, 512),
 ]
 
 

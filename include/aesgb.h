@@ -172,11 +172,16 @@ typedef enum aes_layout {
     AES_LAYOUT_R1 = 1,    /* 1 table per bank-replicated + byte rotations: 64 KiB  */
     AES_LAYOUT_P4 = 2,    /* 4 plain 1 KiB tables in shared memory (bank conflicts) */
     AES_LAYOUT_CONST = 3, /* tables in constant memory, as in the paper (4.2)      */
-    AES_LAYOUT_R4_TMA = 4 /* (plaintext placement, section 4.4) R4 tables; the
+    AES_LAYOUT_R4_TMA = 4,/* (plaintext placement, section 4.4) R4 tables; the
                              plaintext staged into shared memory by
                              TMA bulk copies (two 512 x blocks_per_thread-byte
                              tiles per warp, mbarrier-tracked, two passes ahead)
                              instead of loaded into registers                     */
+    AES_LAYOUT_R2 = 5     /* tables 0 and 1 bank-replicated: 64 KiB (enc) /
+                             96 KiB (dec); tables 2 and 3 are their 16-bit
+                             rotations, applied once per column to the XOR of
+                             the pair's two lookups (eqs (22)-(25): T_k is T_0
+                             rotated by k bytes)                                  */
 } aes_layout;
 
 /* A launch configuration of the ECB kernels. */

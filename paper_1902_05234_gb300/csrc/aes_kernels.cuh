@@ -40,7 +40,7 @@
 
 namespace aesgb {
 
-enum : int { kLayoutR4 = 0, kLayoutR1 = 1, kLayoutP4 = 2, kLayoutConst = 3 };
+enum : int { kLayoutR4 = 0, kLayoutR1 = 1, kLayoutP4 = 2, kLayoutConst = 3, kLayoutR2 = 5 };
 enum : int { kEncrypt = 0, kDecrypt = 1 };
 
 constexpr int kMaxRkWords = 60;  // 4 * (14 + 1)
@@ -60,6 +60,7 @@ struct EcbArgs {
 
 __host__ __device__ constexpr uint32_t table_smem_bytes(int dir, int layout) {
     return layout == kLayoutR4   ? (dir == kDecrypt ? 160u * 1024u : 128u * 1024u)
+           : layout == kLayoutR2 ? (dir == kDecrypt ? 96u * 1024u : 64u * 1024u)
            : layout == kLayoutR1 ? 64u * 1024u
            : layout == kLayoutP4 ? (dir == kDecrypt ? 5u * 1024u : 4u * 1024u)
                                  : 0u;
@@ -127,6 +128,38 @@ template <int DIR> struct Tab<kLayoutR4, DIR> {
     }
 };
 
+// Two bank-replicated tables, T0 and T1, laid out as the first half of R4
+// (64 KiB; decryption adds InvS at 65536 + 128x + 4l).  T2 = rotl(T0, 16)
+// and T3 = rotl(T1, 16), so a column of a round is
+//   T0[a] ^ T1[b] ^ rotl16(T0[c] ^ T1[d] ^ rotr16(k)):
+// one 16-bit rotation per column (kPairRotate) instead of two more tables.
+template <int DIR> struct Tab<kLayoutR2, DIR> {
+    static constexpr int kFinalByte = DIR == kEncrypt ? 1 : 0;
+    static constexpr bool kPairRotate = true;
+    const uint8_t *smem;
+    uint32_t lane4, lane8;
+    __device__ Tab(const uint8_t *s, uint32_t lane) : smem(s), lane4(lane * 4u), lane8(lane * 8u) {}
+    __device__ static void fill(uint8_t *smem, int tid, int nthr) {
+        for (int i = tid; i < 256 * 32; i += nthr) {
+            const int x = i >> 5, l = i & 31;
+            const uint32_t o = static_cast<uint32_t>(x * 256 + l * 4);
+            const uint32_t(*t)[256] = DIR == kEncrypt ? c_tab.te : c_tab.td;
+            sts32(smem, o, t[0][x]);
+            sts32(smem, o + 128u, t[1][x]);
+            if (DIR == kDecrypt)
+                sts32(smem, 65536u + static_cast<uint32_t>(x * 128 + l * 4), c_tab.is[x]);
+        }
+    }
+    // T0 for t = 0, 2 and T1 for t = 1, 3: full_round rotates the t = 2, 3 pair
+    __device__ __forceinline__ uint32_t lookup(int t, uint32_t s, int b) const {
+        return lds32(smem, byte_to_bits8(s, lane4, b) + 128u * (t & 1));
+    }
+    __device__ __forceinline__ uint32_t final_word(uint32_t s, int b) const {
+        if (DIR == kEncrypt) return lds32(smem, byte_to_bits8(s, lane4, b));
+        return lds32(smem, 65536u + (byte_to_bits8(s, lane8, b) >> 1));
+    }
+};
+
 template <int DIR> struct Tab<kLayoutR1, DIR> {
     static constexpr int kFinalByte = DIR == kEncrypt ? 1 : 0;
     const uint8_t *smem;
@@ -185,6 +218,13 @@ template <int DIR> struct Tab<kLayoutConst, DIR> {
 // Rounds
 // ---------------------------------------------------------------------------
 
+// Whether a layout keeps only T0 and T1 (T2, T3 are then their 16-bit rotations).
+template <class TabT, class = void> struct PairRotate { static constexpr bool value = false; };
+template <class TabT> struct PairRotate<TabT, decltype(void(TabT::kPairRotate))> {
+    static constexpr bool value = TabT::kPairRotate;
+};
+template <class TabT> __device__ constexpr bool pair_rotate() { return PairRotate<TabT>::value; }
+
 // Column of the input state whose row-r byte feeds output column j.
 template <int DIR> __device__ constexpr int src_col(int j, int r) {
     return DIR == kEncrypt ? ((j + r) & 3) : ((j - r + 4) & 3);
@@ -197,9 +237,14 @@ __device__ __forceinline__ void full_round(const TabT &tab, uint32_t (&s)[4], co
     uint32_t t[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        uint32_t v = tab.lookup(0, s[src_col<DIR>(j, 0)], 0) ^ tab.lookup(1, s[src_col<DIR>(j, 1)], 1);
-        v ^= tab.lookup(2, s[src_col<DIR>(j, 2)], 2) ^ tab.lookup(3, s[src_col<DIR>(j, 3)], 3);
-        t[j] = v ^ k(kw + j);
+        const uint32_t l0 = tab.lookup(0, s[src_col<DIR>(j, 0)], 0), l1 = tab.lookup(1, s[src_col<DIR>(j, 1)], 1);
+        const uint32_t l2 = tab.lookup(2, s[src_col<DIR>(j, 2)], 2), l3 = tab.lookup(3, s[src_col<DIR>(j, 3)], 3);
+        if constexpr (pair_rotate<TabT>()) {
+            const uint32_t kw16 = __byte_perm(k(kw + j), 0u, 0x1032u);  // rotr16 (= rotl16) of the key word
+            t[j] = l0 ^ l1 ^ __byte_perm(l2 ^ l3 ^ kw16, 0u, 0x1032u);
+        } else {
+            t[j] = (l0 ^ l1) ^ (l2 ^ l3) ^ k(kw + j);
+        }
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) s[j] = t[j];

@@ -11,7 +11,8 @@ namespace aesgb {
 #define AESGB_NR(NR)                                                          \
     AESGB_K(NR, 1, kLayoutR4) AESGB_K(NR, 2, kLayoutR4) AESGB_K(NR, 4, kLayoutR4) \
     AESGB_K(NR, 1, kLayoutR1) AESGB_K(NR, 2, kLayoutR1) AESGB_K(NR, 4, kLayoutR1) \
-    AESGB_K(NR, 1, kLayoutP4) AESGB_K(NR, 1, kLayoutConst)
+    AESGB_K(NR, 1, kLayoutP4) AESGB_K(NR, 1, kLayoutConst) \
+    AESGB_K(NR, 1, kLayoutR2) AESGB_K(NR, 2, kLayoutR2) AESGB_K(NR, 4, kLayoutR2)
 
 AESGB_BOUNDS_READER(ecb_enc)
 

@@ -230,7 +230,7 @@ int aes_tune_ecb(int dir, int nrounds, const uint32_t *rk, const uint8_t *in, ui
     if (st != AES_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     std::vector<aes_launch_cfg> cands;
-    for (int layout : {AES_LAYOUT_R4, AES_LAYOUT_R1})
+    for (int layout : {AES_LAYOUT_R4, AES_LAYOUT_R2, AES_LAYOUT_R1})
         for (int nb : {1, 2, 4})
             for (int th : {128, 256, 512, 768, 1024}) {
                 if (th > (nb >= 4 ? 512 : 1024)) continue;

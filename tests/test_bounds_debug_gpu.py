@@ -59,8 +59,9 @@ def _report(aesgb, what):
 
 def _ecb_cfgs(aesgb):
     out = []
-    for layout in (aesgb.LAYOUT_R4, aesgb.LAYOUT_R1, aesgb.LAYOUT_P4, aesgb.LAYOUT_CONST, aesgb.LAYOUT_R4_TMA):
-        nbs = (1, 2, 4) if layout in (aesgb.LAYOUT_R4, aesgb.LAYOUT_R1, aesgb.LAYOUT_R4_TMA) else (1,)
+    for layout in (aesgb.LAYOUT_R4, aesgb.LAYOUT_R1, aesgb.LAYOUT_P4, aesgb.LAYOUT_CONST, aesgb.LAYOUT_R4_TMA,
+                   aesgb.LAYOUT_R2):
+        nbs = (1, 2, 4) if layout in (aesgb.LAYOUT_R4, aesgb.LAYOUT_R1, aesgb.LAYOUT_R4_TMA, aesgb.LAYOUT_R2) else (1,)
         for nb in nbs:
             for threads in (64, 512, 1024):
                 if nb == 4 and threads > 512:

@@ -47,8 +47,9 @@ def test_edge_sizes_default_cfg(orc, keybits, direction):
 
 def all_cfgs():
     out = []
-    for layout in (aesgb.LAYOUT_R4, aesgb.LAYOUT_R1, aesgb.LAYOUT_P4, aesgb.LAYOUT_CONST, aesgb.LAYOUT_R4_TMA):
-        nbs = (1, 2, 4) if layout in (aesgb.LAYOUT_R4, aesgb.LAYOUT_R1, aesgb.LAYOUT_R4_TMA) else (1,)
+    for layout in (aesgb.LAYOUT_R4, aesgb.LAYOUT_R1, aesgb.LAYOUT_P4, aesgb.LAYOUT_CONST, aesgb.LAYOUT_R4_TMA,
+                   aesgb.LAYOUT_R2):
+        nbs = (1, 2, 4) if layout in (aesgb.LAYOUT_R4, aesgb.LAYOUT_R1, aesgb.LAYOUT_R4_TMA, aesgb.LAYOUT_R2) else (1,)
         for nb in nbs:
             for threads in (64, 256, 512, 1024):
                 if nb == 4 and threads > 512:
@@ -207,7 +208,8 @@ def test_back_to_back_dependent_launches(orc, keybits):
     torch = torch_cuda()
     key = wl.random_key(keybits, 21).tobytes()
     enc, dec, nr = aesgb.aes_expand_key(keybits, key)
-    cfgs = [None, aesgb.make_cfg(1024, 2, aesgb.LAYOUT_R1, 0), aesgb.make_cfg(1024, 2, aesgb.LAYOUT_R4_TMA, 0), "ct"]
+    cfgs = [None, aesgb.make_cfg(1024, 2, aesgb.LAYOUT_R1, 0), aesgb.make_cfg(1024, 2, aesgb.LAYOUT_R4_TMA, 0),
+            aesgb.make_cfg(1024, 2, aesgb.LAYOUT_R2, 0), "ct"]
     k = 12
     for n in (1, 33, 4097, 300_001):
         data = wl.random_bytes(16 * n, 200 + n)

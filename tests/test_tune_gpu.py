@@ -21,7 +21,7 @@ def test_tune_ecb_then_use(orc, tmp_path):
         key = wl.random_key(192, 80).tobytes()
         enc, dec, nr = aesgb.aes_expand_key(192, key)
         best = aesgb.aes_tune_ecb(1, nr, dec, x, y, n)
-        assert best.layout in (0, 1) and best.blocks_per_thread in (1, 2, 4)
+        assert best.layout in (aesgb.LAYOUT_R4, aesgb.LAYOUT_R1, aesgb.LAYOUT_R2) and best.blocks_per_thread in (1, 2, 4)
         assert aesgb.aes_ecb_get_cfg(1, nr, n).as_dict() == best.as_dict()
         aesgb.aes_ecb_decrypt(dec, nr, x, y, n)
         torch.cuda.synchronize()
