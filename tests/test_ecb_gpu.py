@@ -94,6 +94,25 @@ def test_tma_staged_edge_sizes(orc, keybits, direction):
 
 
 @pytest.mark.parametrize("keybits", KEYBITS)
+@pytest.mark.parametrize("direction", [0, 1])
+def test_r2_layout_edge_sizes(orc, keybits, direction):
+    """The two-table layout (T2, T3 as 16-bit rotations of T0, T1) at sizes
+    around a warp's pass of 32 x blocks_per_thread blocks and a CTA's pass,
+    in place and out of place, with guard bytes."""
+    key = wl.random_key(keybits, 12).tobytes()
+    cfgs = (aesgb.make_cfg(1024, 1, aesgb.LAYOUT_R2, 1), aesgb.make_cfg(256, 2, aesgb.LAYOUT_R2, 0),
+            aesgb.make_cfg(512, 4, aesgb.LAYOUT_R2, 1))
+    for cfg in cfgs:
+        for n in (1, 31, 32, 33, 127, 129, 1023, 1025, 4097, 65_537, 300_007):
+            data = wl.random_bytes(16 * n, 200 + n)
+            exp = oracle_ecb(orc, direction, key, data)
+            got, ok = gpu_ecb(direction, key, data, cfg=cfg, guard=64)
+            assert ok and np.array_equal(got, exp), (repr(cfg), n)
+            got, ok = gpu_ecb(direction, key, data, cfg=cfg, inplace=True, guard=64)
+            assert ok and np.array_equal(got, exp), (repr(cfg), n, "in place")
+
+
+@pytest.mark.parametrize("keybits", KEYBITS)
 def test_in_place(orc, keybits):
     key = wl.random_key(keybits, 4).tobytes()
     data = wl.random_bytes(16 * 100_001, 8)
