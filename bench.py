@@ -95,14 +95,20 @@ def workload_config(args, world):
 # ---------------------------------------------------------------------------
 
 class Dist:
-    def __init__(self):
+    """Host-side process group of a multi-GPU run (gloo: barriers and the
+    max / sum over ranks only; no data is exchanged).  Every collective is
+    bounded by `timeout_s`: a rank that died or never arrives makes the others'
+    next collective raise instead of hang."""
+
+    def __init__(self, timeout_s: float = 600.0):
         self.world = int(os.environ.get("WORLD_SIZE", "1"))
         self.rank = int(os.environ.get("RANK", "0"))
         self.local = int(os.environ.get("LOCAL_RANK", "0"))
         self.pg = None
         if self.world > 1:
+            import datetime
             import torch.distributed as dist
-            dist.init_process_group("gloo")
+            dist.init_process_group("gloo", timeout=datetime.timedelta(seconds=timeout_s))
             self.pg = dist
 
     def barrier(self):

@@ -1,6 +1,8 @@
 """The multi-GPU path of bench.py on CPU: two gloo ranks, each with its own
 shard (no data exchanged), the job timed by the slowest rank and credited
-with the work of both -- the weak-scaling aggregation the benchmark reports."""
+with the work of both -- the weak-scaling aggregation the benchmark reports;
+and a rank that leaves before the timing barrier, which must end the other
+rank's barrier with an error within the process-group timeout, not hang it."""
 import os
 import socket
 
@@ -55,3 +57,39 @@ def test_single_rank_aggregation_is_local():
     d = bench.Dist()
     ms, gbps = bench.aggregate_throughput(d, 8.0, 4e9, 4)
     assert ms == 2.0 and gbps == pytest.approx(4e9 / 2e-3 / 1e9)
+
+
+def _leaving_rank_main(rank, world, port, out_q):
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port), "RANK": str(rank),
+                       "WORLD_SIZE": str(world), "LOCAL_RANK": str(rank)})
+    import time
+    import bench
+    d = bench.Dist(timeout_s=5.0)
+    if rank == 1:
+        out_q.put((rank, "left"))       # leaves between steps: never reaches the barrier
+        return
+    t0 = time.monotonic()
+    try:
+        d.barrier()
+        out_q.put((rank, "barrier passed"))
+    except Exception as e:              # the expected outcome: an error, not a hang
+        out_q.put((rank, f"error after {time.monotonic() - t0:.1f} s: {type(e).__name__}"))
+
+
+def test_rank_that_leaves_ends_the_other_ranks_barrier_with_an_error():
+    world = 2
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_leaving_rank_main, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    alive = [p for p in procs if p.is_alive()]
+    for p in alive:
+        p.kill()
+    assert not alive, "a rank hung"
+    res = dict(q.get(timeout=5) for _ in range(world))
+    assert res[1] == "left"
+    assert res[0].startswith("error after"), res[0]
