@@ -352,9 +352,11 @@ int aes_cbc_decrypt(const uint32_t *rk_dec, int nrounds, const uint8_t *iv, cons
 int aes_cfb_decrypt(const uint32_t *rk_enc, int nrounds, const uint8_t *iv, const uint8_t *in, uint8_t *out,
                     size_t nblocks, void *stream);
 
-/* Release every resource the library created lazily (internal streams and
- * events, batch workspaces, tuner state) on all devices.  Call with no work
- * of the library in flight. */
+/* Release every resource the library created lazily on all devices: the
+ * host pipeline's internal streams and events and the library-owned batch
+ * workspaces.  Call with no work of the library in flight.  Later calls
+ * create them again as needed.  Tuned configurations stay (aes_tune_clear
+ * drops them); the fixed scratch of aes_ecb_batch_noalloc lives until exit. */
 int aes_shutdown(void);
 
 /* ------------------------------------------------------------------------ */
