@@ -771,20 +771,28 @@ def run_constant_time(torch, aesgb, src, nbytes, key, keybits, iters=5):
     return {"workload": f"AES-{keybits} ECB, {nbytes // MIB} MiB, bitsliced (no table lookups)", **out}
 
 
-def ct_roofline(aesgb, ct, nbytes, keybits, sms, f_mhz):
+def ct_roofline(aesgb, ct, nbytes, keybits, sms, f_mhz, logic_cal=None):
     """The bitsliced kernel is bound by the integer-logic (ALU) pipe: 64 lanes
     per clock per SM, one 3-input gate or byte permute per lane.  achieved =
     the logic operations its circuits spend per block (aes_ct_ops_per_block,
     counted from the gate tables) x blocks per second; peak = SMs x 64 x the
-    SM clock sampled under load."""
+    SM clock sampled under load.  logic_cal = (ops, seconds) of the LOP3
+    calibration kernel, the measured counterpart of the 64."""
     nr = nrounds_of(keybits)
     peak = sms * 64 * f_mhz * 1e6 / 1e12
     out = {"bound": "alu", "unit": "Tops/s", "peak": round(peak, 2),
            "peak_basis": f"{sms} SMs x 64 logic lanes/clk x {f_mhz:.0f} MHz (median sampled under load)"}
+    if logic_cal is not None:
+        ops, secs = logic_cal
+        out["measured_peak"] = {"tops": round(ops / secs / 1e12, 2),
+                                "lanes_per_clk_per_sm": round(ops / secs / (sms * f_mhz * 1e6), 2),
+                                "source": "aes_calibrate_logic_rate (8 independent LOP3 chains per thread)"}
     for d, name in ((0, "enc"), (1, "dec")):
         ops = aesgb.aes_ct_ops_per_block(d, nr)
         achieved = ops * (nbytes / 16) / (ct[name]["ms"] / 1e3) / 1e12
         out[name] = {"ops_per_block": round(ops, 2), "achieved": round(achieved, 2), "frac": round(achieved / peak, 4)}
+        if logic_cal is not None:
+            out[name]["measured_frac"] = round(achieved / (logic_cal[0] / logic_cal[1] / 1e12), 4)
     return out
 
 
@@ -996,8 +1004,11 @@ def run_gb300(args, dist: Dist):
         line["modes"] = run_modes(torch, aesgb, pt, nbytes, key, args.keybits)
     if dist.rank == 0 and world == 1 and not args.no_ct:
         line["constant_time"] = run_constant_time(torch, aesgb, pt, nbytes, key, args.keybits)
+        sink = torch.empty(sms * 4096, dtype=torch.uint8, device=dev)
+        logic_cal = aesgb.aes_calibrate_logic_rate(sink, sink.numel(), stream)
+        del sink
         line["constant_time"]["roofline"] = ct_roofline(aesgb, line["constant_time"], nbytes, args.keybits,
-                                                        sms, f_mhz)
+                                                        sms, f_mhz, logic_cal)
     if dist.rank == 0 and world == 1 and not args.no_stress:
         line["stress"] = run_stress(torch, aesgb, dev)
     if dist.rank == 0 and world == 1 and not args.no_served:

@@ -537,6 +537,14 @@ int aes_device_sm_count(int device);
  * SM per clock, against the nominal 32. */
 int aes_calibrate_lookup_rate(void *sink_dev, size_t sink_bytes, void *stream, double *lookups, double *seconds);
 
+/* The same for the bound of the constant-time kernel: three-input logic
+ * instructions (LOP3), eight independent chains per thread, one CTA of 1,024
+ * threads per SM.  Returns the thread-level operations performed and the
+ * seconds they took (synchronises `stream`); ops / seconds / (SMs * SM
+ * clock) is the measured peak in lanes per clock per SM, against the nominal
+ * 64.  sink_dev as for aes_calibrate_lookup_rate. */
+int aes_calibrate_logic_rate(void *sink_dev, size_t sink_bytes, void *stream, double *ops, double *seconds);
+
 /* Copy one of the library's 256-entry tables (built at compile time) from
  * HOST memory, no GPU needed:  which = 0 te0 (eq (22) column packed with row r
  * in byte r), 1 td0 (inverse-cipher column 0e/09/0d/0b * InvS), 2 S-box,

@@ -110,6 +110,8 @@ _SIGNATURES = {
     "aes_shutdown": (_i, []),
     "aes_calibrate_lookup_rate": (_i, [_vp, _sz, _vp, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double)]),
+    "aes_calibrate_logic_rate": (_i, [_vp, _sz, _vp, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double)]),
     "aes_ecb_host_direct": (_i, [_i, _u32p, _i, _vp, _vp, _sz, _vp]),
     "aes_ecb_crypt_ct": (_i, [_i, _u32p, _i, _vp, _vp, _sz, _vp]),
     "aes_ct_selftest_host": (_i, [_i, _u32p, _i, _vp, _vp, _sz]),
@@ -517,6 +519,14 @@ def aes_cbc_decrypt(rk_dec, nrounds: int, iv, in_, out, nblocks: int, stream=Non
     v = _block16(iv)
     _check(lib().aes_cbc_decrypt(p, int(nrounds), v.ctypes.data_as(_u8p), _ptr(in_), _ptr(out), int(nblocks),
                                  _stream(stream)), "aes_cbc_decrypt")
+
+
+def aes_calibrate_logic_rate(sink_dev, sink_bytes: int, stream=None) -> tuple[float, float]:
+    """(operations, seconds) of the three-input logic (LOP3) calibration kernel."""
+    n, t = ctypes.c_double(), ctypes.c_double()
+    _check(lib().aes_calibrate_logic_rate(_ptr(sink_dev), int(sink_bytes), _stream(stream), ctypes.byref(n),
+                                          ctypes.byref(t)), "aes_calibrate_logic_rate")
+    return float(n.value), float(t.value)
 
 
 def aes_calibrate_lookup_rate(sink_dev, sink_bytes: int, stream=None) -> tuple[float, float]:

@@ -49,3 +49,21 @@ def test_ct_equals_table_path():
         aesgb.aes_ecb_crypt_ct(1, dec, nr, y2, y2, n)
         torch.cuda.synchronize()
         assert torch.equal(y1, y2) and torch.equal(y1, x)
+
+
+def test_logic_rate_calibration():
+    """The LOP3 calibration kernel measures a rate in the range the hardware
+    allows: positive, and at most 64 lanes per clock per SM at the highest
+    SM clock the device reports (a rate above it would mean the kernel did
+    not do the work it counts)."""
+    torch = torch_cuda()
+    sms = aesgb.aes_device_sm_count(0)
+    sink = torch.empty(sms * 4096, dtype=torch.uint8, device="cuda")
+    ops, secs = aesgb.aes_calibrate_logic_rate(sink, sink.numel())
+    assert ops > 0 and secs > 0
+    clock_hz = torch.cuda.get_device_properties(0).clock_rate * 1e3 if hasattr(
+        torch.cuda.get_device_properties(0), "clock_rate") else 2.1e9
+    per_sm_per_clk = ops / secs / (sms * clock_hz)
+    assert 16 < per_sm_per_clk <= 64 * 1.05, per_sm_per_clk
+    with pytest.raises(aesgb.AesError):
+        aesgb.aes_calibrate_logic_rate(sink, 16)
