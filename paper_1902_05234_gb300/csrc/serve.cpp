@@ -374,7 +374,7 @@ static int submit_locked(Server *s, int key_id, int dir, const uint8_t *in, uint
     if (s->key_nr[key_id] < 0) return AES_E_NOTFOUND;
     if (dir != 0 && dir != 1) return AES_E_ARG;
     if (nbytes % 16) return AES_E_ARG;
-    if (2 * nbytes > s->budget) return AES_E_RANGE;
+    if (nbytes > s->budget / 2) return AES_E_RANGE;  // input + output within the budget (no overflow)
     if (nbytes && (!in || !out)) return AES_E_ARG;
     const int st = check_buffers(in ? in : reinterpret_cast<const uint8_t *>(16),
                                  out ? out : reinterpret_cast<uint8_t *>(16), nbytes / 16);

@@ -131,6 +131,10 @@ def test_errors_and_bounded_wait(server):
         with pytest.raises(aesgb.AesError) as e:
             aesgb.aes_srv_submit(srv2, 0, 0, buf.data_ptr() + 8, buf, 16)
         assert e.value.status == -4
+        # a size whose input + output overflows 64 bits: refused, not admitted as 0 bytes
+        with pytest.raises(aesgb.AesError) as e:
+            aesgb.aes_srv_submit(srv2, 0, 0, buf, buf, 1 << 63)
+        assert e.value.status == -10
         # a request that arrives 30 s from now: a short wait times out on the host
         st, t = aesgb.aes_srv_submit_many(srv2, [0], [0], [buf.data_ptr()], [buf.data_ptr()], [4096], [30.0])
         assert st == 0
