@@ -241,12 +241,17 @@ typedef struct aes_batch_cfg {
  * message order and the chunk prefix: about 20 bytes per descriptor). */
 size_t aes_batch_workspace_bytes(int n);
 
+/* Most descriptors one batch call takes (AES_E_RANGE above it, nothing queued). */
+#define AES_BATCH_MAX_DESCS (1 << 28)
+
 /* Batched ECB with a caller-owned workspace.  Enqueues two kernels on
  * `stream`: a one-CTA plan kernel (validation, encryptions-first order, chunk
- * prefix) and the persistent batch kernel (one CTA per SM; warp g takes chunks
- * g, g+W, ...; a chunk's message is found by binary search; each warp stages
- * its message's round keys in shared memory).  Allocates nothing and never
- * synchronises, so it can be captured in a CUDA graph.
+ * prefix) and the persistent batch kernel (one CTA per SM; each warp takes
+ * the next chunk from an atomic work counter, finds the chunk's message by a
+ * warp-wide 32-ary search of the prefix and stages its round keys through
+ * shared memory into registers).  Allocates nothing and never synchronises,
+ * so it can be captured in a CUDA graph.
+ *   n           0..AES_BATCH_MAX_DESCS.
  *   desc_dev    DEVICE array of n descriptors, unchanged until completion.
  *   ws          DEVICE, 256-byte aligned, ws_bytes >= aes_batch_workspace_bytes(n);
  *               owned by the caller and busy until completion.
@@ -421,8 +426,9 @@ typedef struct aes_srv_stats_t {
 } aes_srv_stats_t;
 
 /* Create a server: key store for max_keys expanded schedules (device),
- * `slots` in-flight batches (1..16), at most max_batch requests per batch.
- * Allocates its device and page-locked memory here (AES_E_NOMEM). */
+ * `slots` in-flight batches (1..16), at most max_batch requests per batch
+ * (1..AES_BATCH_MAX_DESCS, else AES_E_RANGE).  Allocates its device and
+ * page-locked memory here (AES_E_NOMEM). */
 int aes_srv_create(size_t mem_budget_bytes, int max_keys, int max_batch, int slots, aes_server **srv);
 
 /* Expand key (HOST, keybits/8 bytes) and keep both schedules resident under

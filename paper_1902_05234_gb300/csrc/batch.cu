@@ -415,6 +415,7 @@ int validate_batch_cfg(const aes_batch_cfg &c) {
 int enqueue_batch(const aes_desc *desc, int n, void *ws, size_t ws_bytes, int32_t *status,
                   const aes_batch_cfg &c, cudaStream_t s) {
     if (n == 0) return AES_OK;
+    if (n > AES_BATCH_MAX_DESCS) return AES_E_RANGE;  // keeps the kernels' int indices far from overflow
     if (!desc || !ws) return AES_E_ARG;
     if (ws_bytes < batch_ws_bytes(n)) return AES_E_RANGE;
     if (reinterpret_cast<uintptr_t>(ws) & 255u) return AES_E_ALIGN;
@@ -483,6 +484,7 @@ unsigned int batch_chunk_blocks(const aes_batch_cfg &c) {
 // The persistent batch kernel alone, on a workspace planned already.
 int enqueue_batch_kernel(const aes_desc *desc, int n, void *ws, const aes_batch_cfg &c, cudaStream_t s) {
     if (n == 0) return AES_OK;
+    if (n > AES_BATCH_MAX_DESCS) return AES_E_RANGE;
     int st = validate_batch_cfg(c);
     if (st != AES_OK) return st;
     int dev = 0;
@@ -642,6 +644,7 @@ int aes_ecb_batch_ws(const aes_desc *desc_dev, int n, void *ws, size_t ws_bytes,
 int aes_ecb_batch(const aes_desc *desc_dev, int n, void *stream) {
     if (n < 0) return AES_E_ARG;
     if (n == 0) return AES_OK;
+    if (n > AES_BATCH_MAX_DESCS) return AES_E_RANGE;  // before the workspace is sized for it
     int dev = 0;
     if (current_device(&dev) != AES_OK) return AES_E_CUDA;
     void *ws = nullptr;
@@ -672,6 +675,7 @@ int aes_batch_graph_create(const aes_desc *desc_dev, int n, void *ws, size_t ws_
                            const aes_batch_cfg *cfg, aes_batch_graph **out) {
     if (!out || n <= 0) return AES_E_ARG;
     *out = nullptr;
+    if (n > AES_BATCH_MAX_DESCS) return AES_E_RANGE;
     const aes_batch_cfg c = cfg ? *cfg : batch_cfg_for(n);
     int st0 = validate_batch_cfg(c);
     if (st0 != AES_OK) return st0;

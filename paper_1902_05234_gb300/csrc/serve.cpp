@@ -313,6 +313,7 @@ extern "C" {
 int aes_srv_create(size_t mem_budget_bytes, int max_keys, int max_batch, int slots, aes_server **out) {
     if (!out || mem_budget_bytes < 32 || max_keys <= 0 || max_batch <= 0 || slots <= 0 || slots > 16)
         return AES_E_ARG;
+    if (max_batch > AES_BATCH_MAX_DESCS) return AES_E_RANGE;
     *out = nullptr;
     Server *s = new Server();
     s->budget = mem_budget_bytes;

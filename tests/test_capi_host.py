@@ -107,6 +107,20 @@ def test_fail_allocs_hook_arguments(lib):
     assert lib.aes_test_fail_allocs(0, 0) == 0
 
 
+def test_batch_size_above_the_maximum_is_refused_before_any_work(lib):
+    """More than AES_BATCH_MAX_DESCS (2^28) descriptors: AES_E_RANGE from every
+    batch entry point, before any allocation or launch (fake, never used
+    addresses; no device is needed)."""
+    A = 1 << 20
+    n = (1 << 28) + 1
+    assert lib.aes_ecb_batch_ws(A, n, A, 1 << 40, None, None, None) == -10
+    assert lib.aes_ecb_batch(A, n, None) == -10
+    g = ctypes.c_void_p()
+    assert lib.aes_batch_graph_create(A, n, A, 1 << 40, None, None, ctypes.byref(g)) == -10
+    srv = ctypes.c_void_p()
+    assert lib.aes_srv_create(1 << 30, 4, n, 2, ctypes.byref(srv)) == -10
+
+
 def test_server_calls_reject_null_handle(lib):
     assert lib.aes_srv_cancel(None, 1) == -1
     assert lib.aes_srv_register(None, 1 << 20, 4096) == -1
