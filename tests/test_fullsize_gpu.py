@@ -294,6 +294,30 @@ def test_1gib_tma_staged_windows_and_roundtrip(orc, cfg):
 
 
 @pytest.mark.parametrize("keybits", [128, 256])
+@pytest.mark.parametrize("cfg", [(1024, 1), (512, 4)])
+def test_1gib_r2_layout_windows_and_roundtrip(orc, keybits, cfg):
+    """The two-table layout at 1 GiB, both directions: encryption windows
+    against the oracle, decryption in place back to the input."""
+    torch = torch_cuda()
+    nbytes = GIB
+    n = nbytes // 16
+    x = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    _fill_random(torch, x, 74 + keybits)
+    key = wl.random_key(keybits, 74).tobytes()
+    enc, dec, nr = aesgb.aes_expand_key(keybits, key)
+    c = aesgb.make_cfg(cfg[0], cfg[1], aesgb.LAYOUT_R2, 0)
+    y = torch.empty_like(x)
+    aesgb.aes_ecb_crypt_cfg(0, enc, nr, x, y, n, c)
+    torch.cuda.synchronize()
+    win = 64 * 1024
+    for s in _windows(nbytes, win, 75):
+        assert np.array_equal(y[s:s + win].cpu().numpy(), orc.ecb(0, key, x[s:s + win].cpu().numpy(), nthreads=16)), s
+    aesgb.aes_ecb_crypt_cfg(1, dec, nr, y, y, n, c)
+    torch.cuda.synchronize()
+    assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("keybits", [128, 256])
 def test_1gib_ctr_cbc_cfb_windows(orc, keybits):
     """CTR, CBC and CFB decryption at the size the benchmark times them (1 GiB):
     windows against the oracle, each started from its own counter block or
