@@ -361,10 +361,12 @@ def run_reference(args, dist: Dist):
 # GB300 arm
 # ---------------------------------------------------------------------------
 
-def timed_ecb(torch, aesgb, rk, nr, direction, src, dst, nblocks, iters=5, warm=2):
+def timed_ecb(torch, aesgb, rk, nr, direction, src, dst, nblocks, iters=5, warm=2, replays=5):
     """Device time of one launch.  Small buffers take a few microseconds, less
     than a Python call, so the launches are captured in a CUDA graph and the
-    replay is timed: the GPU then runs them back to back."""
+    replay is timed: the GPU then runs them back to back.  The median of
+    `replays` timed replays is taken, so one disturbed replay does not decide
+    a microsecond-scale point."""
     fn = aesgb.aes_ecb_encrypt if direction == 0 else aesgb.aes_ecb_decrypt
     cap = torch.cuda.Stream()
     with torch.cuda.stream(cap):
@@ -377,14 +379,17 @@ def timed_ecb(torch, aesgb, rk, nr, direction, src, dst, nblocks, iters=5, warm=
             fn(rk, nr, src, dst, nblocks, cap)
     g.replay()
     torch.cuda.synchronize()
-    s = torch.cuda.Event(enable_timing=True)
-    e = torch.cuda.Event(enable_timing=True)
-    s.record()
-    g.replay()
-    e.record()
-    e.synchronize()
+    times = []
+    for _ in range(replays):
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record()
+        g.replay()
+        e.record()
+        e.synchronize()
+        times.append(s.elapsed_time(e) / iters)
     del g
-    return s.elapsed_time(e) / iters
+    return statistics.median(times)
 
 
 def run_sweep(torch, aesgb, dev, tune=True):
