@@ -178,7 +178,7 @@ typedef enum aes_layout {
                              tiles per warp, mbarrier-tracked, two passes ahead)
                              instead of loaded into registers                     */
     AES_LAYOUT_R2 = 5     /* tables 0 and 1 bank-replicated: 64 KiB (enc) /
-                             96 KiB (dec); tables 2 and 3 are their 16-bit
+                             128 KiB (dec); tables 2 and 3 are their 16-bit
                              rotations, applied once per column to the XOR of
                              the pair's two lookups (eqs (22)-(25): T_k is T_0
                              rotated by k bytes)                                  */

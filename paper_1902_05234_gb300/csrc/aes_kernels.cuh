@@ -60,7 +60,7 @@ struct EcbArgs {
 
 __host__ __device__ constexpr uint32_t table_smem_bytes(int dir, int layout) {
     return layout == kLayoutR4   ? (dir == kDecrypt ? 160u * 1024u : 128u * 1024u)
-           : layout == kLayoutR2 ? (dir == kDecrypt ? 96u * 1024u : 64u * 1024u)
+           : layout == kLayoutR2 ? (dir == kDecrypt ? 128u * 1024u : 64u * 1024u)
            : layout == kLayoutR1 ? 64u * 1024u
            : layout == kLayoutP4 ? (dir == kDecrypt ? 5u * 1024u : 4u * 1024u)
                                  : 0u;
@@ -129,7 +129,9 @@ template <int DIR> struct Tab<kLayoutR4, DIR> {
 };
 
 // Two bank-replicated tables, T0 and T1, laid out as the first half of R4
-// (64 KiB; decryption adds InvS at 65536 + 128x + 4l).  T2 = rotl(T0, 16)
+// (64 KiB).  Decryption adds InvS at 65536 + 256x + 4l: the same address as
+// the T0 entry plus a constant, so the final round needs no address shift of
+// its own (64 KiB more, with half of each 256-byte row unused).  T2 = rotl(T0, 16)
 // and T3 = rotl(T1, 16), so a column of a round is
 //   T0[a] ^ T1[b] ^ rotl16(T0[c] ^ T1[d] ^ rotr16(k)):
 // one 16-bit rotation per column (kPairRotate) instead of two more tables.
@@ -137,8 +139,8 @@ template <int DIR> struct Tab<kLayoutR2, DIR> {
     static constexpr int kFinalByte = DIR == kEncrypt ? 1 : 0;
     static constexpr bool kPairRotate = true;
     const uint8_t *smem;
-    uint32_t lane4, lane8;
-    __device__ Tab(const uint8_t *s, uint32_t lane) : smem(s), lane4(lane * 4u), lane8(lane * 8u) {}
+    uint32_t lane4;
+    __device__ Tab(const uint8_t *s, uint32_t lane) : smem(s), lane4(lane * 4u) {}
     __device__ static void fill(uint8_t *smem, int tid, int nthr) {
         for (int i = tid; i < 256 * 32; i += nthr) {
             const int x = i >> 5, l = i & 31;
@@ -146,8 +148,7 @@ template <int DIR> struct Tab<kLayoutR2, DIR> {
             const uint32_t(*t)[256] = DIR == kEncrypt ? c_tab.te : c_tab.td;
             sts32(smem, o, t[0][x]);
             sts32(smem, o + 128u, t[1][x]);
-            if (DIR == kDecrypt)
-                sts32(smem, 65536u + static_cast<uint32_t>(x * 128 + l * 4), c_tab.is[x]);
+            if (DIR == kDecrypt) sts32(smem, 65536u + o, c_tab.is[x]);
         }
     }
     // T0 for t = 0, 2 and T1 for t = 1, 3: full_round rotates the t = 2, 3 pair
@@ -155,8 +156,7 @@ template <int DIR> struct Tab<kLayoutR2, DIR> {
         return lds32(smem, byte_to_bits8(s, lane4, b) + 128u * (t & 1));
     }
     __device__ __forceinline__ uint32_t final_word(uint32_t s, int b) const {
-        if (DIR == kEncrypt) return lds32(smem, byte_to_bits8(s, lane4, b));
-        return lds32(smem, 65536u + (byte_to_bits8(s, lane8, b) >> 1));
+        return lds32(smem, byte_to_bits8(s, lane4, b) + (DIR == kEncrypt ? 0u : 65536u));
     }
 };
 
