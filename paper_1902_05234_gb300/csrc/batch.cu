@@ -16,8 +16,10 @@
 //                    chunk).  A chunk's message is found by a warp-wide 32-ary
 //                    search in start[]; its round keys are staged through the
 //                    warp's own shared-memory slot into registers.  The CTA's T tables are filled for
-//                    encryption first and refilled once for decryption, between
-//                    two CTA barriers that every warp reaches.
+//                    encryption first (R4 layout, 128 KiB) and refilled once for
+//                    decryption (R2 layout, also 128 KiB: faster to fill than
+//                    R4's 160 KiB and as fast to use), between two CTA
+//                    barriers that every warp reaches.
 //
 // Workspace layout (caller- or library-owned device memory, see
 // aes_batch_workspace_bytes):
@@ -217,6 +219,11 @@ struct BatchArgs {
 
 constexpr uint32_t kKeySlotBytes = 256;  // 60 words rounded up
 
+// Table layout of each direction's phase; both take 128 KiB.
+template <int DIR> constexpr int kBatchLayout = DIR == kEncrypt ? kLayoutR4 : kLayoutR2;
+constexpr uint32_t kBatchTableBytes = table_smem_bytes(kEncrypt, kLayoutR4);
+static_assert(table_smem_bytes(kDecrypt, kLayoutR2) == kBatchTableBytes, "both phases fit the same tables");
+
 #if defined(AESGB_BOUNDS_CHECK)
 // Debug build: every chunk a warp takes adds one to its tag, so that after one
 // launch each of the T chunks must carry exactly 1 (aes_debug_batch_coverage
@@ -238,7 +245,7 @@ template <int NR> struct RegKey {
 // warp with the next pass prefetched.  The round keys are read once per chunk
 // from the warp's shared-memory slot (16-byte broadcasts) into registers.
 template <int DIR, int NR, int NB>
-__device__ __forceinline__ void batch_chunk(const Tab<kLayoutR4, DIR> &tab, const uint32_t *kslot,
+__device__ __forceinline__ void batch_chunk(const Tab<kBatchLayout<DIR>, DIR> &tab, const uint32_t *kslot,
                                             const uint4 *in, uint4 *out, unsigned long long first,
                                             unsigned long long count, uint32_t lane) {
     RegKey<NR> key;
@@ -303,7 +310,7 @@ template <int DIR, int NB>
 __device__ void batch_phase(const BatchArgs &a, const WsView &v, uint8_t *smem, uint32_t *kslot,
                             unsigned long long c_begin, unsigned long long c_end) {
     const uint32_t lane = threadIdx.x & 31u;
-    const Tab<kLayoutR4, DIR> tab(smem, lane);
+    const Tab<kBatchLayout<DIR>, DIR> tab(smem, lane);
     unsigned long long *counter = &v.hdr->next[DIR];
     const unsigned long long nchunks = c_end - c_begin;
     const unsigned int cb = v.hdr->chunk_blocks;
@@ -374,16 +381,15 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(const __grid
     extern __shared__ __align__(128) uint8_t smem[];
     const WsView v = ws_view(a.ws, a.n);
     const unsigned long long T = v.hdr->total_chunks, E = v.hdr->enc_chunks;
-    uint32_t *kslot = reinterpret_cast<uint32_t *>(smem + table_smem_bytes(kDecrypt, kLayoutR4) +
-                                                   (threadIdx.x >> 5) * kKeySlotBytes);
+    uint32_t *kslot = reinterpret_cast<uint32_t *>(smem + kBatchTableBytes + (threadIdx.x >> 5) * kKeySlotBytes);
     if (E > 0) {
-        Tab<kLayoutR4, kEncrypt>::fill(smem, threadIdx.x, blockDim.x);
+        Tab<kBatchLayout<kEncrypt>, kEncrypt>::fill(smem, threadIdx.x, blockDim.x);
         __syncthreads();
         batch_phase<kEncrypt, NB>(a, v, smem, kslot, 0, E);
     }
     if (T > E) {
         __syncthreads();  // every warp is done with the encryption tables
-        Tab<kLayoutR4, kDecrypt>::fill(smem, threadIdx.x, blockDim.x);
+        Tab<kBatchLayout<kDecrypt>, kDecrypt>::fill(smem, threadIdx.x, blockDim.x);
         __syncthreads();
         batch_phase<kDecrypt, NB>(a, v, smem, kslot, E, T);
     }
@@ -392,7 +398,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(const __grid
 AESGB_BOUNDS_READER(batch)
 
 uint32_t batch_smem_bytes(int threads) {
-    return table_smem_bytes(kDecrypt, kLayoutR4) + static_cast<uint32_t>(threads / 32) * kKeySlotBytes;
+    return kBatchTableBytes + static_cast<uint32_t>(threads / 32) * kKeySlotBytes;
 }
 
 const void *batch_kernel_ptr(int nb) {
