@@ -262,10 +262,24 @@ int aes_ecb_batch_ws(const aes_desc *desc_dev, int n, void *ws, size_t ws_bytes,
                      const aes_batch_cfg *cfg, void *stream);
 
 /* Batched ECB with a library-owned workspace: the same as aes_ecb_batch_ws
- * with a per-device workspace the library allocates on first use and grows
- * (cudaMalloc; the growth synchronises the device) when n exceeds it; freed by
- * aes_shutdown.  Concurrent batches on different streams of one device must
- * use aes_ecb_batch_ws with distinct workspaces. */
+ * (default configuration, no status array) with a workspace the library keeps
+ * per (device, stream) -- streams told apart by their CUDA stream id, so each
+ * host thread's per-thread default stream has its own.  The workspace is
+ * allocated on the first call on a stream (at least 1 MiB) and grown when n
+ * needs more.  Allocation and growth are stream-ordered (cudaMallocAsync /
+ * cudaFreeAsync on `stream`): the call never synchronises the device nor
+ * waits for other streams, and the buffer it replaces is released only after
+ * the batches already queued on `stream`.  Calls may come from several host
+ * threads at once, on the same or on different streams; calls on different
+ * streams never share a workspace.  Workspaces are freed by aes_shutdown; once
+ * more than 64 exist, the idle ones (last batch complete) of other streams are
+ * released when a new stream makes one.
+ *   desc_dev  DEVICE array of n descriptors (NULL with n > 0: AES_E_ARG).
+ * AES_E_NOMEM if the workspace cannot be allocated (nothing is enqueued, the
+ * stream's old workspace stays).  A stream that is being captured into a CUDA
+ * graph is refused with AES_E_CONFIG, nothing enqueued: the graph would keep
+ * the address of a workspace that a later call on the stream may release --
+ * capture aes_ecb_batch_ws with a caller-owned workspace instead. */
 int aes_ecb_batch(const aes_desc *desc_dev, int n, void *stream);
 
 /* Batched ECB that allocates nothing: not even the workspace.  The paper has
@@ -410,8 +424,13 @@ int aes_ct_selftest_host(int dir, const uint32_t *rk, int nrounds, const uint8_t
  * validated at submission) and launches it on that slot's stream (descriptor
  * and plan upload, the persistent batch kernel, completion event).  Requests
  * that arrive while earlier batches run join the next batch; consecutive
- * batches overlap on the device.  Host waits are bounded; nothing waits on the
- * device.  Latency = host arrival -> host-observed completion.
+ * batches overlap on the device.  A batch's device interval runs from the
+ * moment its stream reaches the kernel (descriptors uploaded, two events
+ * bound it) to the kernel's completion; aes_srv_stats reports how many such
+ * intervals overlapped at most, and for how long.  The dispatcher holds the
+ * server's lock only to pack and to retire batches, never across CUDA calls.
+ * Host waits are bounded; nothing waits on the device.  Latency = host
+ * arrival -> host-observed completion.
  * A server handle is used from one host thread at a time (plus its own
  * dispatcher); it works on the device that was current at creation. */
 typedef struct aes_server aes_server;
@@ -423,6 +442,13 @@ typedef struct aes_srv_stats_t {
     int32_t worker_status;  /* AES_OK, or the first dispatcher CUDA error   */
     int32_t reserved;
     uint64_t cancelled;     /* requests completed by aes_srv_cancel         */
+    uint64_t peak_busy_slots;     /* most slots holding a launched, not yet
+                                     retired batch at once (host view)       */
+    uint64_t timed_batches;       /* batches whose device interval was taken */
+    uint64_t peak_device_batches; /* most batches whose device intervals
+                                     contain one instant                      */
+    double device_overlap_s;      /* time in which two or more batches'
+                                     device intervals overlap                 */
 } aes_srv_stats_t;
 
 /* Create a server: key store for max_keys expanded schedules (device),
@@ -432,13 +458,19 @@ typedef struct aes_srv_stats_t {
 int aes_srv_create(size_t mem_budget_bytes, int max_keys, int max_batch, int slots, aes_server **srv);
 
 /* Expand key (HOST, keybits/8 bytes) and keep both schedules resident under
- * key_id (0..max_keys-1); synchronous.  Replace a key only while no request
- * using it is in flight. */
+ * key_id (0..max_keys-1).  The upload runs on a stream of the server's own,
+ * and every batch launched afterwards waits for it on the device; the call
+ * returns once the bytes are staged, without waiting for the device.
+ * Replacing a key that a queued or in-flight request names is refused with
+ * AES_E_BUSY (the request would otherwise run with the new key): drain or
+ * cancel those requests first.  While the upload is being issued, submissions
+ * naming key_id answer AES_E_BUSY.  AES_E_CUDA if the upload fails. */
 int aes_srv_put_key(aes_server *srv, int key_id, int keybits, const uint8_t *key);
 
 /* Submit one request arriving now: in_dev/out_dev DEVICE, 16-byte aligned,
  * equal or disjoint, nbytes a multiple of 16 with 2*nbytes <= budget
- * (AES_E_RANGE), key_id resident (AES_E_NOTFOUND).  *ticket identifies it. */
+ * (AES_E_RANGE), key_id resident (AES_E_NOTFOUND; AES_E_BUSY while
+ * aes_srv_put_key is uploading it).  *ticket identifies it. */
 int aes_srv_submit(aes_server *srv, int key_id, int dir, const uint8_t *in_dev, uint8_t *out_dev,
                    size_t nbytes, uint64_t *ticket);
 

@@ -71,7 +71,9 @@ class aes_srv_stats_t(ctypes.Structure):
                 ("bytes_completed", ctypes.c_uint64), ("inflight_bytes", ctypes.c_uint64),
                 ("peak_inflight_bytes", ctypes.c_uint64), ("pending", ctypes.c_uint64),
                 ("busy_s", ctypes.c_double), ("worker_status", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("cancelled", ctypes.c_uint64)]
+                ("cancelled", ctypes.c_uint64), ("peak_busy_slots", ctypes.c_uint64),
+                ("timed_batches", ctypes.c_uint64), ("peak_device_batches", ctypes.c_uint64),
+                ("device_overlap_s", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}

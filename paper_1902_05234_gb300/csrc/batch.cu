@@ -28,7 +28,10 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <map>
+#include <memory>
 #include <mutex>
+#include <utility>
 
 #include "aesgb.h"
 #include "aes_kernels.cuh"
@@ -511,44 +514,123 @@ int enqueue_batch_kernel(const aes_desc *desc, int n, void *ws, const aes_batch_
 }
 
 // ---------------------------------------------------------------------------
-// library-owned workspace for aes_ecb_batch (grown on demand, per device)
+// library-owned workspaces for aes_ecb_batch: one per (device, stream)
 // ---------------------------------------------------------------------------
+// A stream is named by its CUDA stream id (cudaStreamGetId), which is unique
+// for the process's lifetime and tells apart the per-thread default streams
+// that share one handle value.  Work on one stream runs in order, so a
+// workspace reused by the next call on the same stream is never in use by
+// another batch; calls on different streams never share one.  Growth is
+// stream-ordered: the old buffer goes back with cudaFreeAsync behind the
+// batches already enqueued on that stream, the new one comes from
+// cudaMallocAsync, and neither waits for the device.  A context's mutex is
+// held from the size check to the end of the enqueue, so no thread can free a
+// buffer that another thread has looked up but not yet enqueued.
 namespace {
-constexpr int kMaxDev = 64;
-struct LibWs {
+struct StreamWs {
     std::mutex mu;
     void *ptr = nullptr;
     size_t bytes = 0;
+    int dev = 0;
+    cudaEvent_t last = nullptr;  // recorded after the newest batch that uses ptr
 };
-LibWs g_ws[kMaxDev];
+using WsKey = std::pair<int, unsigned long long>;  // device, stream id
+std::mutex g_ws_mu;
+std::map<WsKey, std::shared_ptr<StreamWs>> g_ws;
+// Above this many contexts, idle ones (last batch complete) are released
+// when a new one is made: streams the caller destroyed leave contexts behind.
+constexpr size_t kMaxStreamWs = 64;
+
+// Release the device memory of contexts other than `keep` whose last batch
+// has completed (g_ws_mu held).  The memory is idle, so it goes back in the
+// order of stream s without waiting for anything.
+void evict_idle_locked(const StreamWs *keep, cudaStream_t s) {
+    for (auto it = g_ws.begin(); it != g_ws.end() && g_ws.size() > kMaxStreamWs;) {
+        StreamWs &w = *it->second;
+        std::unique_lock<std::mutex> lk(w.mu, std::try_to_lock);
+        const bool idle = &w != keep && lk.owns_lock() &&
+                          (w.last == nullptr || cudaEventQuery(w.last) == cudaSuccess);
+        (void)cudaGetLastError();
+        if (!idle) {
+            ++it;
+            continue;
+        }
+        if (w.ptr) (void)cudaFreeAsync(w.ptr, s);
+        if (w.last) (void)cudaEventDestroy(w.last);
+        w.ptr = nullptr;
+        w.bytes = 0;
+        w.last = nullptr;
+        lk.unlock();
+        it = g_ws.erase(it);
+    }
+    (void)cudaGetLastError();
+}
 }  // namespace
 
-int lib_workspace(int dev, size_t need, void **ptr) {
-    LibWs &w = g_ws[dev];
-    std::lock_guard<std::mutex> lk(w.mu);
+// The context of (dev, stream s), created on first use.
+int stream_workspace(int dev, cudaStream_t s, std::shared_ptr<StreamWs> *out) {
+    unsigned long long id = 0;
+    if (cudaStreamGetId(s, &id) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return AES_E_CUDA;
+    }
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    std::shared_ptr<StreamWs> &slot = g_ws[WsKey{dev, id}];
+    if (!slot) {
+        slot = std::make_shared<StreamWs>();
+        slot->dev = dev;
+    }
+    *out = slot;  // (evict_idle_locked keeps this entry, so the reference stays valid)
+    if (g_ws.size() > kMaxStreamWs) evict_idle_locked(out->get(), s);
+    return AES_OK;
+}
+
+// Enqueue the batch on s with the context's workspace, grown first if it is
+// smaller than `need` (w.mu held by the caller).
+int enqueue_with_stream_ws(StreamWs &w, const aes_desc *desc, int n, size_t need, cudaStream_t s) {
     if (w.bytes < need) {
-        if (w.ptr) {
-            if (cudaDeviceSynchronize() != cudaSuccess) return AES_E_CUDA;  // the old one may be in use
-            cudaFree(w.ptr);
-            w.ptr = nullptr;
-            w.bytes = 0;
-        }
-        size_t sz = need < (1u << 20) ? (1u << 20) : need * 2;
-        const int st = lib_malloc_device(&w.ptr, sz);
-        if (st != AES_OK) return st;
+        const size_t sz = need < (1u << 20) ? (1u << 20) : need * 2;
+        void *p = nullptr;
+        const int st = lib_malloc_device_async(&p, sz, s);
+        if (st != AES_OK) return st;  // the old workspace stays as it was
+        if (w.ptr) (void)cudaFreeAsync(w.ptr, s);
+        w.ptr = p;
         w.bytes = sz;
     }
-    *ptr = w.ptr;
+    if (!w.last && cudaEventCreateWithFlags(&w.last, cudaEventDisableTiming) != cudaSuccess) {
+        (void)cudaGetLastError();
+        w.last = nullptr;
+        return AES_E_CUDA;
+    }
+    const int st = enqueue_batch(desc, n, w.ptr, w.bytes, nullptr, batch_cfg_for(n), s);
+    if (st != AES_OK) return st;
+    if (cudaEventRecord(w.last, s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return AES_E_CUDA;
+    }
     return AES_OK;
 }
 
 void batch_shutdown() {
-    for (int d = 0; d < kMaxDev; ++d) {
-        std::lock_guard<std::mutex> lk(g_ws[d].mu);
-        if (g_ws[d].ptr) cudaFree(g_ws[d].ptr);
-        g_ws[d].ptr = nullptr;
-        g_ws[d].bytes = 0;
+    std::map<WsKey, std::shared_ptr<StreamWs>> all;
+    {
+        std::lock_guard<std::mutex> lk(g_ws_mu);
+        all.swap(g_ws);
     }
+    int cur = 0;
+    const bool have_cur = cudaGetDevice(&cur) == cudaSuccess;
+    for (auto &kv : all) {
+        StreamWs &w = *kv.second;
+        std::lock_guard<std::mutex> lk(w.mu);
+        if (w.ptr || w.last) (void)cudaSetDevice(w.dev);
+        if (w.ptr) (void)cudaFree(w.ptr);  // no library work is in flight (aes_shutdown's contract)
+        if (w.last) (void)cudaEventDestroy(w.last);
+        w.ptr = nullptr;
+        w.bytes = 0;
+        w.last = nullptr;
+    }
+    if (have_cur) (void)cudaSetDevice(cur);
+    (void)cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -573,6 +655,7 @@ constexpr size_t kNoAllocBytes = noalloc_scratch_bytes(AES_BATCH_NOALLOC_MAX_DES
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocBytes];
 
 namespace {
+constexpr int kMaxDev = 64;
 std::mutex g_noalloc_mu;
 void *g_noalloc_addr[kMaxDev];  // device address of g_noalloc_scratch, per device
 }  // namespace
@@ -651,13 +734,23 @@ int aes_ecb_batch(const aes_desc *desc_dev, int n, void *stream) {
     if (n < 0) return AES_E_ARG;
     if (n == 0) return AES_OK;
     if (n > AES_BATCH_MAX_DESCS) return AES_E_RANGE;  // before the workspace is sized for it
+    if (!desc_dev) return AES_E_ARG;
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // a graph captured from this call would keep the workspace's address after
+    // a later call on the stream has replaced it: capture aes_ecb_batch_ws
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return AES_E_CUDA;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return AES_E_CONFIG;
     int dev = 0;
     if (current_device(&dev) != AES_OK) return AES_E_CUDA;
-    void *ws = nullptr;
-    const size_t need = batch_ws_bytes(n);
-    int st = lib_workspace(dev, need, &ws);
+    std::shared_ptr<StreamWs> w;
+    const int st = stream_workspace(dev, s, &w);
     if (st != AES_OK) return st;
-    return enqueue_batch(desc_dev, n, ws, need, nullptr, batch_cfg_for(n), static_cast<cudaStream_t>(stream));
+    std::lock_guard<std::mutex> lk(w->mu);
+    return enqueue_with_stream_ws(*w, desc_dev, n, batch_ws_bytes(n), s);
 }
 
 int aes_ecb_batch_noalloc(const aes_desc *desc_dev, int n, int32_t *status_dev, void *stream) {

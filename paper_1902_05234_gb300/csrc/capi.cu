@@ -202,6 +202,17 @@ int lib_malloc_device(void **p, size_t bytes) {
     return AES_OK;
 }
 
+int lib_malloc_device_async(void **p, size_t bytes, cudaStream_t s) {
+    *p = nullptr;
+    if (take_injected_failure()) return AES_E_NOMEM;
+    if (cudaMallocAsync(p, bytes, s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        *p = nullptr;
+        return AES_E_NOMEM;
+    }
+    return AES_OK;
+}
+
 int lib_malloc_host(void **p, size_t bytes) {
     *p = nullptr;
     if (take_injected_failure()) return AES_E_NOMEM;

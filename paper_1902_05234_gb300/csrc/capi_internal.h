@@ -3,6 +3,8 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda_runtime.h>
+
 #include "aesgb.h"
 
 namespace aesgb {
@@ -22,6 +24,8 @@ int check_nrounds(int nr);
 // AES_E_NOMEM with *p = nullptr.
 int lib_malloc_device(void **p, size_t bytes);
 int lib_malloc_host(void **p, size_t bytes);
+// Stream-ordered device allocation (cudaMallocAsync on s), same injector.
+int lib_malloc_device_async(void **p, size_t bytes, cudaStream_t s);
 int check_buffers(const void *in, const void *out, size_t nblocks);
 void order_round_keys(int dir, const uint32_t *rk, int nr, RoundKeys *out);
 int validate_cfg(const aes_launch_cfg &c);

@@ -16,6 +16,15 @@
 //     on the device;
 //   * retires a slot when its event has completed: the requests' statuses and
 //     completion times are recorded and their bytes leave the budget.
+// The dispatcher holds the server's mutex only while it picks a slot and packs
+// requests, and while it retires slots; the plan, the upload and the launch run
+// outside it, so submissions and polls never wait behind CUDA calls.  Keys are
+// uploaded on a server-owned stream; a batch's stream waits for the newest
+// upload (an event) before its kernel.  A key that a queued or in-flight request
+// names cannot be replaced.  For each batch two events bound its device
+// interval: from the moment its stream reaches the kernel (descriptors
+// uploaded) to the kernel's completion; the intervals show how many batches
+// were on the device at once.
 // Host waits are bounded (condition variables with timeouts); nothing on the
 // device waits.  Latency is host arrival -> host-observed completion.
 // Queued requests can be cancelled; an optional registry of device ranges
@@ -67,7 +76,9 @@ struct Req {
 
 struct Slot {
     cudaStream_t stream = nullptr;
-    cudaEvent_t ev = nullptr;
+    cudaEvent_t ev = nullptr;        // after the batch kernel
+    cudaEvent_t ev_start = nullptr;  // before it: the stream has reached the batch
+    uint64_t key_gen_seen = 0;       // key uploads this slot's stream has waited for
     // One page-locked buffer and its device copy per slot, uploaded with one
     // copy per batch: n descriptors at the start, the host-built plan (the
     // batch kernel's workspace) at the next 256-byte boundary.
@@ -85,6 +96,11 @@ struct Server {
     int max_keys = 0, max_batch = 0;
     uint32_t *d_rk_enc = nullptr, *d_rk_dec = nullptr;  // max_keys x 64 words
     std::vector<int> key_nr;
+    std::vector<uint32_t> key_users;  // queued or in-flight requests naming each key
+    std::vector<char> key_updating;   // an upload of this key is in progress
+    cudaStream_t key_stream = nullptr;
+    cudaEvent_t key_ev = nullptr;     // recorded after the newest key upload
+    uint64_t key_gen = 0;             // key uploads so far
     std::vector<Slot> slots;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -110,18 +126,62 @@ struct Server {
     // statistics
     uint64_t n_submitted = 0, n_completed = 0, n_batches = 0, bytes_completed = 0, n_cancelled = 0;
     double first_arrival = 0, last_done = 0;
+    size_t peak_busy = 0;  // most slots busy at once
+    // Device intervals of the batches of the current busy period (from the
+    // launch that found every slot idle until all are retired again), in
+    // seconds after `ref`, an event recorded at the period's first launch.
+    cudaEvent_t ref = nullptr;
+    std::vector<std::pair<double, double>> period_iv;
+    uint64_t timed_batches = 0, peak_dev = 0;
+    double overlap_s = 0;
 };
+
+// Largest number of intervals that contain one instant, and the time covered
+// by two or more of them (a sweep over the sorted ends; an end before a start
+// at the same instant).
+std::pair<uint64_t, double> sweep(const std::vector<std::pair<double, double>> &iv) {
+    std::vector<std::pair<double, int>> ev;
+    ev.reserve(2 * iv.size());
+    for (const auto &x : iv) {
+        ev.emplace_back(x.first, +1);
+        ev.emplace_back(x.second, -1);
+    }
+    std::sort(ev.begin(), ev.end());
+    uint64_t peak = 0;
+    int cur = 0;
+    double two = 0, last = 0;
+    for (const auto &e : ev) {
+        if (cur >= 2) two += e.first - last;
+        last = e.first;
+        cur += e.second;
+        if (cur > 0 && static_cast<uint64_t>(cur) > peak) peak = static_cast<uint64_t>(cur);
+    }
+    return {peak, two};
+}
+
+// Fold the finished busy period's intervals into the totals (mu held).
+void fold_period_locked(Server *s) {
+    const auto r = sweep(s->period_iv);
+    s->peak_dev = std::max(s->peak_dev, r.first);
+    s->overlap_s += r.second;
+    s->period_iv.clear();
+}
 
 constexpr uint32_t kRkStrideWords = 64;
 
 void free_server(Server *s) {
+    if (s->key_stream) cudaStreamSynchronize(s->key_stream);
     for (Slot &sl : s->slots) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);
         if (sl.ev) cudaEventDestroy(sl.ev);
+        if (sl.ev_start) cudaEventDestroy(sl.ev_start);
         if (sl.stream) cudaStreamDestroy(sl.stream);
         if (sl.h_desc) cudaFreeHost(sl.h_desc);
         if (sl.d_desc) cudaFree(sl.d_desc);
     }
+    if (s->key_ev) cudaEventDestroy(s->key_ev);
+    if (s->key_stream) cudaStreamDestroy(s->key_stream);
+    if (s->ref) cudaEventDestroy(s->ref);
     if (s->d_rk_enc) cudaFree(s->d_rk_enc);
     if (s->d_rk_dec) cudaFree(s->d_rk_dec);
     delete s;
@@ -175,10 +235,18 @@ void retire_locked(Server *s) {
         const double t = now_s();
         const bool ok = q == cudaSuccess;
         if (!ok) (void)cudaGetLastError();
+        float a = 0.f, b = 0.f;
+        if (ok && cudaEventElapsedTime(&a, s->ref, sl.ev_start) == cudaSuccess &&
+            cudaEventElapsedTime(&b, s->ref, sl.ev) == cudaSuccess) {
+            s->period_iv.emplace_back(1e-3 * a, 1e-3 * b);
+            s->timed_batches++;
+        }
+        (void)cudaGetLastError();
         for (size_t i = 0; i < sl.tickets.size(); ++i) {
             Req *rp = s->find(sl.tickets[i]);
             if (!rp) continue;
             Req &r = *rp;
+            s->key_users[r.key_id]--;
             r.done = true;
             r.done_t = t;
             r.status = ok ? AES_OK : AES_E_CUDA;  // requests were validated at submission
@@ -193,12 +261,26 @@ void retire_locked(Server *s) {
     }
 }
 
-// Admit and launch one batch on a free slot (mu held).  Returns true if a
-// batch was launched.
-bool dispatch_locked(Server *s, int sms) {
+// A batch packed under the mutex, to be planned and launched without it.
+struct Launch {
     Slot *sl = nullptr;
-    for (Slot &x : s->slots)
-        if (!x.busy) { sl = &x; break; }
+    int n = 0;
+    unsigned long long blocks = 0;
+    bool new_period = false;  // every other slot was idle: the batch opens a busy period
+    bool wait_keys = false;   // keys were uploaded since this slot's stream last waited
+};
+
+// Admit requests into a free slot's descriptors (mu held).  The slot is marked
+// busy and its bytes counted in flight before the mutex is released, so that
+// nothing else takes the slot or the budget; only the dispatcher thread
+// touches slots.  Returns false if there is no free slot or nothing to admit.
+bool pack_locked(Server *s, Launch *L) {
+    Slot *sl = nullptr;
+    size_t busy = 0;
+    for (Slot &x : s->slots) {
+        if (x.busy) ++busy;
+        else if (!sl) sl = &x;
+    }
     if (!sl || s->pending.empty()) return false;
     const double t = now_s();
     int n = 0;
@@ -231,38 +313,65 @@ bool dispatch_locked(Server *s, int sms) {
         ++n;
     }
     if (n == 0) return false;
-    const NvtxRange range("aes_srv plan+launch");
-    // the plan (message order, chunk prefix, zeroed counters) is built here on
-    // the host -- every request was validated at submission -- and uploaded
-    // with the descriptors, so only the persistent kernel runs on the device
-    const aes_batch_cfg cfg = serve_cfg(sms, blocks);
-    const size_t ws_off = plan_offset(n);
-    plan_on_host(sl->h_desc, n, batch_chunk_blocks(cfg), reinterpret_cast<uint8_t *>(sl->h_desc) + ws_off);
-    bool ok = cudaMemcpyAsync(sl->d_desc, sl->h_desc, ws_off + batch_ws_bytes(n), cudaMemcpyHostToDevice,
-                              sl->stream) == cudaSuccess;
-    ok = ok && enqueue_batch_kernel(sl->d_desc, n, reinterpret_cast<uint8_t *>(sl->d_desc) + ws_off, cfg,
-                                    sl->stream) == AES_OK;
-    ok = ok && cudaEventRecord(sl->ev, sl->stream) == cudaSuccess;
-    if (!ok) {
-        (void)cudaGetLastError();
-        s->worker_error = AES_E_CUDA;
-        // the event may not have been recorded: mark the batch done now
-        for (size_t i = 0; i < sl->tickets.size(); ++i) {
-            Req &r = *s->find(sl->tickets[i]);
-            r.done = true;
-            r.done_t = now_s();
-            r.status = AES_E_CUDA;
-            s->n_completed++;
-        }
-        sl->tickets.clear();
-        return true;
-    }
+    if (busy == 0) fold_period_locked(s);  // the previous busy period has ended
     sl->busy = true;
     sl->bytes = bytes;
     s->inflight += bytes;
     s->peak_inflight = std::max(s->peak_inflight, s->inflight);
-    s->n_batches++;
+    s->peak_busy = std::max(s->peak_busy, busy + 1);
+    L->sl = sl;
+    L->n = n;
+    L->blocks = blocks;
+    L->new_period = busy == 0;
+    L->wait_keys = sl->key_gen_seen < s->key_gen;
+    sl->key_gen_seen = s->key_gen;
     return true;
+}
+
+// Plan the packed batch on the host and launch it on the slot's stream (mu
+// NOT held): the plan (message order, chunk prefix, zeroed counters) is built
+// here -- every request was validated at submission -- and uploaded with the
+// descriptors, so only the persistent kernel runs on the device.
+bool launch_unlocked(Server *s, const Launch &L, int sms) {
+    const NvtxRange range("aes_srv plan+launch");
+    Slot *sl = L.sl;
+    const aes_batch_cfg cfg = serve_cfg(sms, L.blocks);
+    const size_t ws_off = plan_offset(L.n);
+    plan_on_host(sl->h_desc, L.n, batch_chunk_blocks(cfg), reinterpret_cast<uint8_t *>(sl->h_desc) + ws_off);
+    bool ok = !L.new_period || cudaEventRecord(s->ref, sl->stream) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(sl->d_desc, sl->h_desc, ws_off + batch_ws_bytes(L.n), cudaMemcpyHostToDevice,
+                               sl->stream) == cudaSuccess;
+    ok = ok && (!L.wait_keys || cudaStreamWaitEvent(sl->stream, s->key_ev, 0) == cudaSuccess);
+    ok = ok && cudaEventRecord(sl->ev_start, sl->stream) == cudaSuccess;
+    ok = ok && enqueue_batch_kernel(sl->d_desc, L.n, reinterpret_cast<uint8_t *>(sl->d_desc) + ws_off, cfg,
+                                    sl->stream) == AES_OK;
+    ok = ok && cudaEventRecord(sl->ev, sl->stream) == cudaSuccess;
+    if (!ok) (void)cudaGetLastError();
+    return ok;
+}
+
+// Count a launched batch, or complete its requests with AES_E_CUDA if the
+// launch failed (mu held).
+void finish_launch_locked(Server *s, const Launch &L, bool ok) {
+    Slot *sl = L.sl;
+    if (ok) {
+        s->n_batches++;
+        return;
+    }
+    s->worker_error = AES_E_CUDA;
+    // the event may not have been recorded: mark the batch done now
+    for (size_t i = 0; i < sl->tickets.size(); ++i) {
+        Req &r = *s->find(sl->tickets[i]);
+        s->key_users[r.key_id]--;
+        r.done = true;
+        r.done_t = now_s();
+        r.status = AES_E_CUDA;
+        s->n_completed++;
+    }
+    sl->tickets.clear();
+    s->inflight -= sl->bytes;
+    sl->bytes = 0;
+    sl->busy = false;
 }
 
 void worker_main(Server *s) {
@@ -280,7 +389,14 @@ void worker_main(Server *s) {
         const uint64_t before = s->n_completed;
         retire_locked(s);
         bool launched = false;
-        while (dispatch_locked(s, sms)) launched = true;
+        Launch L;
+        while (!s->stop && pack_locked(s, &L)) {
+            lk.unlock();
+            const bool ok = launch_unlocked(s, L, sms);
+            lk.lock();
+            finish_launch_locked(s, L, ok);
+            launched = true;
+        }
         if (s->n_completed != before) s->cv_done.notify_all();
         bool any_busy = false;
         for (const Slot &sl : s->slots) any_busy |= sl.busy;
@@ -320,6 +436,8 @@ int aes_srv_create(size_t mem_budget_bytes, int max_keys, int max_batch, int slo
     s->max_keys = max_keys;
     s->max_batch = max_batch;
     s->key_nr.assign(static_cast<size_t>(max_keys), -1);
+    s->key_users.assign(static_cast<size_t>(max_keys), 0u);
+    s->key_updating.assign(static_cast<size_t>(max_keys), 0);
     int st = current_device(&s->dev);
     const size_t rk_bytes = static_cast<size_t>(max_keys) * kRkStrideWords * 4;
     void *rk_enc = nullptr, *rk_dec = nullptr;
@@ -327,13 +445,19 @@ int aes_srv_create(size_t mem_budget_bytes, int max_keys, int max_batch, int slo
               (st = lib_malloc_device(&rk_dec, rk_bytes)) == AES_OK;
     s->d_rk_enc = static_cast<uint32_t *>(rk_enc);
     s->d_rk_dec = static_cast<uint32_t *>(rk_dec);
+    if (ok && (cudaStreamCreateWithFlags(&s->key_stream, cudaStreamNonBlocking) != cudaSuccess ||
+               cudaEventCreateWithFlags(&s->key_ev, cudaEventDisableTiming) != cudaSuccess ||
+               cudaEventCreate(&s->ref) != cudaSuccess)) {
+        ok = false;
+        st = AES_E_CUDA;
+    }
     s->slots.resize(static_cast<size_t>(slots));
     for (Slot &sl : s->slots) {
         if (!ok) break;
         sl.buf_bytes = plan_offset(max_batch) + aes_batch_workspace_bytes(max_batch);
         void *hb = nullptr, *db = nullptr;
         ok = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) == cudaSuccess &&
-             cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) == cudaSuccess;
+             cudaEventCreate(&sl.ev) == cudaSuccess && cudaEventCreate(&sl.ev_start) == cudaSuccess;
         if (!ok) st = AES_E_CUDA;
         ok = ok && (st = lib_malloc_host(&hb, sl.buf_bytes)) == AES_OK &&
              (st = lib_malloc_device(&db, sl.buf_bytes)) == AES_OK;
@@ -357,21 +481,41 @@ int aes_srv_put_key(aes_server *h, int key_id, int keybits, const uint8_t *key) 
     uint32_t enc[kRkStrideWords] = {0}, dec[kRkStrideWords] = {0};
     const int nr = expand_key_host(keybits, key, enc, dec);
     if (nr < 0) return nr;
-    const size_t off = static_cast<size_t>(key_id) * kRkStrideWords;
-    std::lock_guard<std::mutex> lk(s->mu);
-    cudaSetDevice(s->dev);
-    if (cudaMemcpy(s->d_rk_enc + off, enc, sizeof enc, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(s->d_rk_dec + off, dec, sizeof dec, cudaMemcpyHostToDevice) != cudaSuccess) {
-        (void)cudaGetLastError();
-        return AES_E_CUDA;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        // a queued or launched request would otherwise run with the new key
+        if (s->key_users[key_id] > 0 || s->key_updating[key_id]) return AES_E_BUSY;
+        s->key_updating[key_id] = 1;  // submissions naming it answer AES_E_BUSY meanwhile
     }
-    s->key_nr[key_id] = nr;
-    return AES_OK;
+    // Upload on the server's key stream, outside the mutex.  The sources are
+    // pageable, so each copy returns once its bytes are staged; the event
+    // orders the upload before the next batch of every slot.
+    const size_t off = static_cast<size_t>(key_id) * kRkStrideWords;
+    int prev = 0;
+    const bool have_prev = cudaGetDevice(&prev) == cudaSuccess;
+    bool ok = cudaSetDevice(s->dev) == cudaSuccess &&
+              cudaMemcpyAsync(s->d_rk_enc + off, enc, sizeof enc, cudaMemcpyHostToDevice, s->key_stream) ==
+                  cudaSuccess &&
+              cudaMemcpyAsync(s->d_rk_dec + off, dec, sizeof dec, cudaMemcpyHostToDevice, s->key_stream) ==
+                  cudaSuccess &&
+              cudaEventRecord(s->key_ev, s->key_stream) == cudaSuccess;
+    if (!ok) (void)cudaGetLastError();
+    if (have_prev) (void)cudaSetDevice(prev);
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->key_updating[key_id] = 0;
+        if (ok) {
+            s->key_nr[key_id] = nr;
+            s->key_gen++;
+        }
+    }
+    return ok ? AES_OK : AES_E_CUDA;
 }
 
 static int submit_locked(Server *s, int key_id, int dir, const uint8_t *in, uint8_t *out, size_t nbytes,
                          double arrival, uint64_t *ticket) {
     if (key_id < 0 || key_id >= s->max_keys) return AES_E_NOTFOUND;
+    if (s->key_updating[key_id]) return AES_E_BUSY;
     if (s->key_nr[key_id] < 0) return AES_E_NOTFOUND;
     if (dir != 0 && dir != 1) return AES_E_ARG;
     if (nbytes % 16) return AES_E_ARG;
@@ -392,6 +536,7 @@ static int submit_locked(Server *s, int key_id, int dir, const uint8_t *in, uint
     r.arrival = arrival;
     s->reqs.push_back(r);
     s->pending.push_back(t);
+    s->key_users[key_id]++;
     if (s->n_submitted == 0 || arrival < s->first_arrival) s->first_arrival = arrival;
     s->n_submitted++;
     *ticket = t;
@@ -518,6 +663,7 @@ int aes_srv_cancel(aes_server *h, uint64_t ticket) {
         const auto it = std::find(s->pending.begin(), s->pending.end(), ticket);
         if (r->done || it == s->pending.end()) return AES_E_BUSY;
         s->pending.erase(it);
+        s->key_users[r->key_id]--;
         r->done = true;
         r->done_t = now_s();
         r->admitted = r->done_t;
@@ -569,6 +715,11 @@ int aes_srv_stats(aes_server *h, aes_srv_stats_t *out) {
     out->worker_status = s->worker_error;
     out->reserved = 0;
     out->cancelled = s->n_cancelled;
+    out->peak_busy_slots = s->peak_busy;
+    out->timed_batches = s->timed_batches;
+    const auto cur = sweep(s->period_iv);  // the busy period still open
+    out->peak_device_batches = std::max(s->peak_dev, cur.first);
+    out->device_overlap_s = s->overlap_s + cur.second;
     return AES_OK;
 }
 

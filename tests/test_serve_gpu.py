@@ -81,6 +81,153 @@ def test_served_mix_matches_oracle_and_alone(orc, server):
         assert np.array_equal(a.msg(alone_h, i), a.msg(out, i)), i
 
 
+def _check_windows(orc, key, dirn, src, got, whole=64 * 1024, win=2048):
+    """A served result against the oracle: whole up to `whole` bytes, else its
+    first and last `win` bytes (ECB is blockwise)."""
+    if src.size <= whole:
+        return np.array_equal(got, orc.ecb(dirn, key, src, nthreads=1))
+    return all(np.array_equal(got[w], orc.ecb(dirn, key, src[w], nthreads=1))
+               for w in (slice(0, win), slice(src.size - win, src.size)))
+
+
+def test_served_workload_ranges_match_oracle_and_alone(orc):
+    """The served workload's ranges: request sizes log-uniform from 64 B to
+    4 MiB, 1,024 resident keys of mixed size, Poisson arrivals, a 4 GiB
+    budget over 4 slots.  Every result against the oracle (whole up to
+    64 KiB, the first and last 2 KiB above), and a sample re-run alone into
+    fresh buffers is identical to its result in the mix."""
+    torch = torch_cuda()
+    srv = aesgb.aes_srv_create(4 << 30, max_keys=1024, max_batch=4096, slots=4)
+    try:
+        g = wl.rng(75)
+        keys = {}
+        for k in range(1024):
+            kb = int(g.choice(np.array([128, 192, 256])))
+            keys[k] = g.integers(0, 256, kb // 8, dtype=np.uint8).tobytes()
+            aesgb.aes_srv_put_key(srv, k, kb, keys[k])
+        n = 800
+        arrivals, sizes, key_ids, dirs = wl.served_workload(n, rate_per_s=20000.0, n_keys=1024, seed_offset=76)
+        assert sizes.min() >= 64 and sizes.max() <= 4 << 20 and sizes.max() > 1 << 20
+        a = Arena(torch, sizes, 77)
+        st, tickets = aesgb.aes_srv_submit_many(srv, key_ids, dirs, a.ins(), a.outs(), sizes,
+                                                arrivals - arrivals[0])
+        assert st == 0 and np.all(tickets > 0)
+        aesgb.aes_srv_drain(srv, 120000)
+        status, lat, _ = aesgb.aes_srv_results(srv, tickets)
+        assert np.all(status == 0) and np.all(lat > 0)
+        out = a.out.cpu().numpy()
+        for i in range(n):
+            key = keys[int(key_ids[i])]
+            assert _check_windows(orc, key, int(dirs[i]), a.msg(a.data, i), a.msg(out, i)), i
+        stats = aesgb.aes_srv_stats(srv)
+        assert stats["completed"] == n and stats["worker_status"] == 0
+        assert 0 < stats["peak_inflight_bytes"] <= 4 << 30
+        alone = torch.full_like(a.out, 0x33)
+        outs_alone = a.outs(alone)
+        sample = list(range(0, n, 37)) + [int(np.argmax(sizes))]
+        for i in sample:
+            t = aesgb.aes_srv_submit(srv, int(key_ids[i]), int(dirs[i]), int(a.ins()[i]), int(outs_alone[i]),
+                                     int(sizes[i]))
+            s_, _ = aesgb.aes_srv_wait(srv, t, 10000)
+            assert s_ == 0
+        alone_h = alone.cpu().numpy()
+        for i in sample:
+            assert np.array_equal(a.msg(alone_h, i), a.msg(out, i)), i
+    finally:
+        aesgb.aes_srv_destroy(srv)
+
+
+def test_batches_overlap_on_the_device(orc):
+    """Continuous batching: a 1 GiB AES-256 request takes one slot, and small
+    requests that arrive while it runs are packed into batches on the other
+    slots.  The stats show two or more slots busy at once and, from the
+    batches' device intervals, a later batch's stream reaching its kernel
+    before the long batch's kernel completed.  Every result equals the oracle
+    (the long one in windows) and its re-run alone."""
+    torch = torch_cuda()
+    srv = aesgb.aes_srv_create(4 << 30, max_keys=4, max_batch=1024, slots=4)
+    try:
+        keys = {k: wl.random_key((256, 128, 192, 256)[k], 410 + k).tobytes() for k in range(4)}
+        for k in range(4):
+            aesgb.aes_srv_put_key(srv, k, 8 * len(keys[k]), keys[k])
+        big_n = 1 << 30
+        gen = torch.Generator(device="cuda").manual_seed(190205230 + 411)
+        big_in = torch.randint(0, 256, (big_n,), dtype=torch.uint8, device="cuda", generator=gen)
+        big_out = torch.full_like(big_in, 0x5A)
+        m = 240
+        g = wl.rng(412)
+        sizes = wl.log_uniform_lengths(m, 64, 64 * 1024, g)
+        kid = g.integers(0, 4, size=m)
+        dirs = g.integers(0, 2, size=m)
+        a = Arena(torch, sizes, 413)
+        offsets = np.concatenate([[0.0], np.linspace(1e-4, 2e-3, m)])   # small ones over 2 ms
+        ins = np.concatenate([[big_in.data_ptr()], a.ins()]).astype(np.uint64)
+        outs = np.concatenate([[big_out.data_ptr()], a.outs()]).astype(np.uint64)
+        st, tickets = aesgb.aes_srv_submit_many(srv, np.concatenate([[0], kid]), np.concatenate([[1], dirs]),
+                                                ins, outs, np.concatenate([[big_n], sizes]), offsets)
+        assert st == 0 and np.all(tickets > 0)
+        aesgb.aes_srv_drain(srv, 60000)
+        status, _, _ = aesgb.aes_srv_results(srv, tickets)
+        assert np.all(status == 0)
+        stats = aesgb.aes_srv_stats(srv)
+        assert stats["batches"] >= 3 and stats["timed_batches"] == stats["batches"]
+        assert stats["peak_busy_slots"] >= 2, stats
+        assert stats["peak_device_batches"] >= 2 and stats["device_overlap_s"] > 0, stats
+        out = a.out.cpu().numpy()
+        for i in range(m):
+            assert _check_windows(orc, keys[int(kid[i])], int(dirs[i]), a.msg(a.data, i), a.msg(out, i)), i
+        for off in (0, big_n // 2 - 4096, big_n - 65536):
+            w = slice(off, off + 65536)
+            src = big_in[w].cpu().numpy()
+            assert np.array_equal(big_out[w].cpu().numpy(), orc.ecb(1, keys[0], src, nthreads=4)), off
+        # alone: the long request and every 9th small one, into fresh buffers
+        big_alone = torch.full_like(big_in, 0x33)
+        t = aesgb.aes_srv_submit(srv, 0, 1, big_in, big_alone, big_n)
+        s_, _ = aesgb.aes_srv_wait(srv, t, 20000)
+        assert s_ == 0 and torch.equal(big_alone, big_out)
+        alone = torch.full_like(a.out, 0x33)
+        for i in range(0, m, 9):
+            t = aesgb.aes_srv_submit(srv, int(kid[i]), int(dirs[i]), int(a.ins()[i]), int(a.outs(alone)[i]),
+                                     int(sizes[i]))
+            s_, _ = aesgb.aes_srv_wait(srv, t, 10000)
+            assert s_ == 0
+        alone_h = alone.cpu().numpy()
+        for i in range(0, m, 9):
+            assert np.array_equal(a.msg(alone_h, i), a.msg(out, i)), i
+    finally:
+        aesgb.aes_srv_destroy(srv)
+
+
+def test_put_key_refused_while_a_request_names_it(orc):
+    """A queued request keeps its key: replacing the key it names answers
+    AES_E_BUSY until the request is gone (here: cancelled).  The replacement,
+    of another size, is then used by the next request, and other keys can be
+    replaced meanwhile."""
+    torch = torch_cuda()
+    srv = aesgb.aes_srv_create(8 << 20, max_keys=2, max_batch=16, slots=2)
+    try:
+        k128, k256 = wl.random_key(128, 420).tobytes(), wl.random_key(256, 421).tobytes()
+        aesgb.aes_srv_put_key(srv, 0, 128, k128)
+        aesgb.aes_srv_put_key(srv, 1, 128, k128)
+        data = wl.random_bytes(1 << 16, 422)
+        x = torch.from_numpy(data).cuda()
+        y = torch.full_like(x, 0x5A)
+        st, t = aesgb.aes_srv_submit_many(srv, [0], [0], [x.data_ptr()], [y.data_ptr()], [data.size], [30.0])
+        assert st == 0
+        with pytest.raises(aesgb.AesError) as e:
+            aesgb.aes_srv_put_key(srv, 0, 256, k256)          # the queued request names key 0
+        assert e.value.status == -9
+        aesgb.aes_srv_put_key(srv, 1, 256, k256)              # key 1 is free to change
+        aesgb.aes_srv_cancel(srv, int(t[0]))
+        aesgb.aes_srv_put_key(srv, 0, 256, k256)
+        t2 = aesgb.aes_srv_submit(srv, 0, 0, x, y, data.size)
+        s_, _ = aesgb.aes_srv_wait(srv, t2, 10000)
+        assert s_ == 0
+        assert np.array_equal(y.cpu().numpy(), orc.ecb(0, k256, data, nthreads=4))
+    finally:
+        aesgb.aes_srv_destroy(srv)
+
+
 def test_budget_caps_bytes_in_flight(orc, server):
     torch = torch_cuda()
     srv0, keys = server
