@@ -690,6 +690,10 @@ STUDY_VARIANTS = [  # (label, layout, blocks/thread, threads)
     ("shared, 2 replicated tables + one rotation per column, 16 B/thread", 5, 1, 1024),
     ("shared, 2 replicated tables + one rotation per column, 32 B/thread", 5, 2, 1024),
     ("shared, 2 replicated tables + one rotation per column, 64 B/thread", 5, 4, 512),
+    ("shared, 4 replicated tables, 128 B/thread", 0, 8, 256),
+    ("shared, 2 replicated tables + one rotation per column, 128 B/thread", 5, 8, 256),
+    ("registers, T0 spread over the warp's lanes, shuffles + selects, 16 B/thread", 6, 1, 256),
+    ("registers, T0 spread over the warp's lanes, shuffles + selects, 32 B/thread", 6, 2, 256),
 ]
 
 

@@ -177,19 +177,28 @@ typedef enum aes_layout {
                              TMA bulk copies (two 512 x blocks_per_thread-byte
                              tiles per warp, mbarrier-tracked, two passes ahead)
                              instead of loaded into registers                     */
-    AES_LAYOUT_R2 = 5     /* tables 0 and 1 bank-replicated: 64 KiB (enc) /
+    AES_LAYOUT_R2 = 5,    /* tables 0 and 1 bank-replicated: 64 KiB (enc) /
                              128 KiB (dec); tables 2 and 3 are their 16-bit
                              rotations, applied once per column to the XOR of
                              the pair's two lookups (eqs (22)-(25): T_k is T_0
                              rotated by k bytes)                                  */
+    AES_LAYOUT_REG = 6    /* the table in registers (section 4.2's third
+                             placement): each warp's 32 lanes hold the 256
+                             entries of T0, eight each; a lookup gathers the
+                             eight candidates from one lane by warp shuffles
+                             and selects one; T1..T3 by byte rotation.  No
+                             shared memory; blocks_per_thread 1 or 2, at
+                             most 256 threads                                  */
 } aes_layout;
 
 /* A launch configuration of the ECB kernels. */
 typedef struct aes_launch_cfg {
     int32_t threads;           /* threads per CTA, multiple of 32, 32..1024
-                                  (<= 512 when blocks_per_thread is 4)          */
-    int32_t blocks_per_thread; /* AES blocks per thread per pass: 1, 2 or 4
-                                  (granularity 16, 32 or 64 bytes per thread)   */
+                                  (<= 512 when blocks_per_thread is 4, <= 256
+                                  when it is 8)                                 */
+    int32_t blocks_per_thread; /* AES blocks per thread per pass: 1, 2, 4 or 8
+                                  (granularity 16, 32, 64 or 128 bytes per
+                                  thread; 8 with layouts R4 and R2 only)        */
     int32_t layout;            /* aes_layout                                     */
     int32_t ctas_per_sm;       /* persistent grid = ctas_per_sm x SM count;
                                   0 = as many as fit                             */

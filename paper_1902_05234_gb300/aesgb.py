@@ -27,8 +27,8 @@ LIB_PATH = os.path.join(_HERE, "libaesgb_debug.so" if os.environ.get("AESGB_LIBR
 _lib = None
 _lock = threading.Lock()
 
-LAYOUT_R4, LAYOUT_R1, LAYOUT_P4, LAYOUT_CONST, LAYOUT_R4_TMA, LAYOUT_R2 = 0, 1, 2, 3, 4, 5
-LAYOUT_NAMES = {0: "R4", 1: "R1", 2: "P4", 3: "CONST", 4: "R4_TMA", 5: "R2"}
+LAYOUT_R4, LAYOUT_R1, LAYOUT_P4, LAYOUT_CONST, LAYOUT_R4_TMA, LAYOUT_R2, LAYOUT_REG = 0, 1, 2, 3, 4, 5, 6
+LAYOUT_NAMES = {0: "R4", 1: "R1", 2: "P4", 3: "CONST", 4: "R4_TMA", 5: "R2", 6: "REG"}
 ENCRYPT, DECRYPT = 0, 1
 
 

@@ -26,6 +26,13 @@
 //   P4  four plain 1 KiB tables (t*1024 + 4x): the paper's "shared memory"
 //       alternative of section 4.2, with bank conflicts.
 //   CONST  the tables in constant memory, as the paper places them (4.2).
+//   REG  the table in registers, the third placement of section 4.2: lane l
+//       of every warp holds T0[l + 32j], j = 0..7, in eight registers.  A
+//       lookup of x takes register j from lane x mod 32 by shuffle, for all
+//       eight j (a shuffle reads the same register in every source lane), and
+//       keeps j = x / 32 with three selects; T1..T3 are byte rotations of T0.
+//       Decryption adds InvS, four bytes per register (two registers).  No
+//       shared memory.
 //
 // Round keys are uniform across the grid (section 4.3 puts them in constant
 // memory): the single-buffer kernels take them as kernel parameters, so each
@@ -40,7 +47,7 @@
 
 namespace aesgb {
 
-enum : int { kLayoutR4 = 0, kLayoutR1 = 1, kLayoutP4 = 2, kLayoutConst = 3, kLayoutR2 = 5 };
+enum : int { kLayoutR4 = 0, kLayoutR1 = 1, kLayoutP4 = 2, kLayoutConst = 3, kLayoutR2 = 5, kLayoutReg = 6 };
 enum : int { kEncrypt = 0, kDecrypt = 1 };
 
 constexpr int kMaxRkWords = 60;  // 4 * (14 + 1)
@@ -66,10 +73,41 @@ __host__ __device__ constexpr uint32_t table_smem_bytes(int dir, int layout) {
                                  : 0u;
 }
 
-constexpr int max_threads_for_nb(int nb) { return nb >= 4 ? 512 : 1024; }
+constexpr int max_threads_for_nb(int nb) { return nb >= 8 ? 256 : nb >= 4 ? 512 : 1024; }
+// The register-table layout holds eight (decryption ten) table words per
+// thread, and the compiler keeps the shuffled candidates of several lookups
+// live at once: at most 256 threads (up to 255 registers each; at 512 threads
+// it spills).
+constexpr int max_threads_for(int nb, int layout) {
+    return layout == kLayoutReg && max_threads_for_nb(nb) > 256 ? 256 : max_threads_for_nb(nb);
+}
 
 // Each module keeps its own copy of the compile-time tables in constant memory.
 static __constant__ ConstTables c_tab = make_const_tables();
+
+// The same T0 and D0, and InvS packed four bytes per word (byte k of word w is
+// InvS[4w + k]), in global memory for the shared-memory table fills and the
+// register layout: a warp reads each with coalesced loads (one 128-byte line
+// per register), where constant memory would serve 32 different addresses one
+// at a time.  Compile-time constants, never written, so a kernel may read them
+// before it waits for the previous kernel in its stream.
+struct FillTables {
+    uint32_t t0[2][256];
+    uint32_t is4[64];
+};
+constexpr FillTables make_fill_tables() {
+    FillTables f{};
+    for (int x = 0; x < 256; ++x) {
+        f.t0[0][x] = kAes.te0[x];
+        f.t0[1][x] = kAes.td0[x];
+    }
+    for (int w = 0; w < 64; ++w)
+        f.is4[w] = static_cast<uint32_t>(kAes.isbox[4 * w]) | (static_cast<uint32_t>(kAes.isbox[4 * w + 1]) << 8) |
+                   (static_cast<uint32_t>(kAes.isbox[4 * w + 2]) << 16) |
+                   (static_cast<uint32_t>(kAes.isbox[4 * w + 3]) << 24);
+    return f;
+}
+static __device__ const FillTables g_fill = make_fill_tables();
 
 // Table reads and writes at a byte offset into the dynamic shared memory
 // (checked against the launch's size in the debug build).
@@ -94,6 +132,38 @@ __device__ __forceinline__ uint32_t byte_of(uint32_t s, int b) {
     return __byte_perm(s, 0u, 0x4440u | static_cast<uint32_t>(b));
 }
 
+// Fill of the bank-replicated layouts (R4, R2, R1).  Warp w loads T0 (D0)
+// into eight registers per lane (entry lane + 32j in register j) and InvS into
+// two; then for every entry x = 32j + c with c = w, w + nw, ... it broadcasts
+// T0[x] (and InvS[x]) from lane c by shuffle, and each lane l calls
+// put(x, l, T0[x], InvS[x]) to store the entry into its own replicas, which
+// sit in bank l: a warp's stores never conflict, and no lane waits on a
+// constant-cache load per entry.  T1..T3 are rotations of T0 (eqs
+// (22)-(25)), so put() derives them.  Every thread of the CTA calls this
+// (full-warp shuffles); nthr is a multiple of 32, at most 1024.
+template <int DIR, class Put>
+__device__ __forceinline__ void fill_replicated(int tid, int nthr, Put put) {
+    const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+    uint32_t r[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) r[j] = g_fill.t0[DIR][lane + 32 * j];
+    const uint32_t is0 = DIR == kDecrypt ? g_fill.is4[lane] : 0u;
+    const uint32_t is1 = DIR == kDecrypt ? g_fill.is4[lane + 32] : 0u;
+    for (int c = warp; c < 32; c += nw) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint32_t x = 32u * j + static_cast<uint32_t>(c);
+            const uint32_t t0 = __shfl_sync(0xffffffffu, r[j], c);
+            uint32_t is = 0u;
+            if (DIR == kDecrypt) {  // packed word x / 4 sits in lane (x / 4) mod 32 of is0 (x < 128) or is1
+                const uint32_t wv = __shfl_sync(0xffffffffu, j < 4 ? is0 : is1, static_cast<int>((x >> 2) & 31u));
+                is = (wv >> (8u * (x & 3u))) & 0xffu;
+            }
+            put(x, static_cast<uint32_t>(lane), t0, is);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Table policies.  lookup(t, s, b): table t at index byte b of word s.
 // final_word(s, b): a word whose byte kFinalByte is S(x) (encrypt) or IS(x)
@@ -107,17 +177,14 @@ template <int DIR> struct Tab<kLayoutR4, DIR> {
     uint32_t lane4, lane8;
     __device__ Tab(const uint8_t *s, uint32_t lane) : smem(s), lane4(lane * 4u), lane8(lane * 8u) {}
     __device__ static void fill(uint8_t *smem, int tid, int nthr) {
-        for (int i = tid; i < 256 * 32; i += nthr) {
-            const int x = i >> 5, l = i & 31;
-            const uint32_t o = static_cast<uint32_t>(x * 256 + l * 4);
-            const uint32_t(*t)[256] = DIR == kEncrypt ? c_tab.te : c_tab.td;
-            sts32(smem, o, t[0][x]);
-            sts32(smem, o + 128u, t[1][x]);
-            sts32(smem, o + 65536u, t[2][x]);
-            sts32(smem, o + 65536u + 128u, t[3][x]);
-            if (DIR == kDecrypt)
-                sts32(smem, 131072u + static_cast<uint32_t>(x * 128 + l * 4), c_tab.is[x]);
-        }
+        fill_replicated<DIR>(tid, nthr, [smem](uint32_t x, uint32_t l, uint32_t t0, uint32_t is) {
+            const uint32_t o = x * 256u + l * 4u;
+            sts32(smem, o, t0);
+            sts32(smem, o + 128u, rotl32(t0, 8));
+            sts32(smem, o + 65536u, rotl32(t0, 16));
+            sts32(smem, o + 65536u + 128u, rotl32(t0, 24));
+            if (DIR == kDecrypt) sts32(smem, 131072u + x * 128u + l * 4u, is);
+        });
     }
     __device__ __forceinline__ uint32_t lookup(int t, uint32_t s, int b) const {
         return lds32(smem, byte_to_bits8(s, lane4, b) + 128u * (t & 1) + 65536u * (t >> 1));
@@ -142,14 +209,12 @@ template <int DIR> struct Tab<kLayoutR2, DIR> {
     uint32_t lane4;
     __device__ Tab(const uint8_t *s, uint32_t lane) : smem(s), lane4(lane * 4u) {}
     __device__ static void fill(uint8_t *smem, int tid, int nthr) {
-        for (int i = tid; i < 256 * 32; i += nthr) {
-            const int x = i >> 5, l = i & 31;
-            const uint32_t o = static_cast<uint32_t>(x * 256 + l * 4);
-            const uint32_t(*t)[256] = DIR == kEncrypt ? c_tab.te : c_tab.td;
-            sts32(smem, o, t[0][x]);
-            sts32(smem, o + 128u, t[1][x]);
-            if (DIR == kDecrypt) sts32(smem, 65536u + o, c_tab.is[x]);
-        }
+        fill_replicated<DIR>(tid, nthr, [smem](uint32_t x, uint32_t l, uint32_t t0, uint32_t is) {
+            const uint32_t o = x * 256u + l * 4u;
+            sts32(smem, o, t0);
+            sts32(smem, o + 128u, rotl32(t0, 8));
+            if (DIR == kDecrypt) sts32(smem, 65536u + o, is);
+        });
     }
     // T0 for t = 0, 2 and T1 for t = 1, 3: full_round rotates the t = 2, 3 pair
     __device__ __forceinline__ uint32_t lookup(int t, uint32_t s, int b) const {
@@ -166,12 +231,11 @@ template <int DIR> struct Tab<kLayoutR1, DIR> {
     uint32_t lane4;
     __device__ Tab(const uint8_t *s, uint32_t lane) : smem(s), lane4(lane * 4u) {}
     __device__ static void fill(uint8_t *smem, int tid, int nthr) {
-        for (int i = tid; i < 256 * 32; i += nthr) {
-            const int x = i >> 5, l = i & 31;
-            const uint32_t o = static_cast<uint32_t>(x * 256 + l * 4);
-            sts32(smem, o, DIR == kEncrypt ? c_tab.te[0][x] : c_tab.td[0][x]);
-            if (DIR == kDecrypt) sts32(smem, o + 128u, c_tab.is[x]);
-        }
+        fill_replicated<DIR>(tid, nthr, [smem](uint32_t x, uint32_t l, uint32_t t0, uint32_t is) {
+            const uint32_t o = x * 256u + l * 4u;
+            sts32(smem, o, t0);
+            if (DIR == kDecrypt) sts32(smem, o + 128u, is);
+        });
     }
     __device__ __forceinline__ uint32_t lookup(int t, uint32_t s, int b) const {
         return rotl32(lds32(smem, byte_to_bits8(s, lane4, b)), 8 * t);
@@ -211,6 +275,41 @@ template <int DIR> struct Tab<kLayoutConst, DIR> {
     }
     __device__ __forceinline__ uint32_t final_word(uint32_t s, int b) const {
         return DIR == kEncrypt ? c_tab.te[0][byte_of(s, b)] : c_tab.is[byte_of(s, b)];
+    }
+};
+
+template <int DIR> struct Tab<kLayoutReg, DIR> {
+    static constexpr int kFinalByte = DIR == kEncrypt ? 1 : 0;
+    uint32_t t[8];   // T0[lane + 32j] (D0 for decryption)
+    uint32_t is[2];  // decryption: InvS bytes 4w..4w+3, w = lane + 32j, byte k at bits 8k..8k+7
+    __device__ Tab(const uint8_t *, uint32_t lane) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) t[j] = g_fill.t0[DIR][lane + 32 * j];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) is[j] = DIR == kEncrypt ? 0u : g_fill.is4[lane + 32 * j];
+    }
+    __device__ static void fill(uint8_t *, int, int) {}
+    // T0[x]: every lane of the warp calls this together (full-warp shuffles)
+    __device__ __forceinline__ uint32_t get(uint32_t x) const {
+        const int src = static_cast<int>(x & 31u);
+        uint32_t v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = __shfl_sync(0xffffffffu, t[j], src);
+        const bool b5 = (x & 32u) != 0u, b6 = (x & 64u) != 0u, b7 = (x & 128u) != 0u;
+        const uint32_t a0 = b5 ? v[1] : v[0], a1 = b5 ? v[3] : v[2], a2 = b5 ? v[5] : v[4], a3 = b5 ? v[7] : v[6];
+        const uint32_t c0 = b6 ? a1 : a0, c1 = b6 ? a3 : a2;
+        return b7 ? c1 : c0;
+    }
+    __device__ __forceinline__ uint32_t lookup(int t_, uint32_t s, int b) const {
+        return rotl32(get(byte_of(s, b)), 8 * t_);
+    }
+    __device__ __forceinline__ uint32_t final_word(uint32_t s, int b) const {
+        const uint32_t x = byte_of(s, b);
+        if (DIR == kEncrypt) return get(x);
+        const uint32_t w = x >> 2;
+        const uint32_t v0 = __shfl_sync(0xffffffffu, is[0], static_cast<int>(w & 31u));
+        const uint32_t v1 = __shfl_sync(0xffffffffu, is[1], static_cast<int>(w & 31u));
+        return ((w & 32u) ? v1 : v0) >> (8u * (x & 3u));
     }
 };
 
@@ -306,20 +405,40 @@ __device__ __forceinline__ uint4 ld_block(const uint4 *p) { return __ldcs(p); }
 __device__ __forceinline__ void st_block(uint4 *p, uint4 v) { __stcs(p, v); }
 
 // ---------------------------------------------------------------------------
-// Single-buffer ECB kernel (persistent, grid-stride).  Warp w of the grid owns
-// blocks [base, base + 32*NB) of each pass, lane l blocks base + l + 32*i, so
-// every warp-wide 128-bit load/store covers 512 contiguous bytes.  The next
-// pass's blocks are loaded before the current ones are ciphered.
+// Single-buffer ECB kernel (persistent).  A warp's unit of work is 32*NB
+// consecutive blocks, lane l taking blocks base + l + 32*i, so every
+// warp-wide 128-bit load/store covers 512 contiguous bytes; the next unit's
+// blocks are loaded before the current ones are ciphered.  Units are assigned
+// in one of two ways, decided per launch (the same in every warp):
+//  * at most kEvenSplitUnits units per warp (small buffers): warp w of W takes
+//    the contiguous units [w*U/W, (w+1)*U/W), so every SM gets the same work
+//    within one unit per warp and no launch ends on a partly filled pass;
+//  * otherwise grid-stride passes: warp w takes units w, w + W, w + 2W, ...,
+//    so the grid sweeps the buffer front to back (at most one pass of
+//    imbalance among hundreds).
 // ---------------------------------------------------------------------------
+constexpr unsigned long long kEvenSplitUnits = 8;
+
 template <int DIR, int NR, int NB, int LAYOUT>
-__global__ void __launch_bounds__(max_threads_for_nb(NB), 1)
+__global__ void __launch_bounds__(max_threads_for(NB, LAYOUT), 1)
     ecb_kernel(const __grid_constant__ EcbArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t lane = threadIdx.x & 31u;
-    const unsigned long long n = a.nblocks;
     const unsigned long long wpc = blockDim.x >> 5;
-    const unsigned long long step = static_cast<unsigned long long>(gridDim.x) * wpc * 32ull * NB;
-    unsigned long long base = (blockIdx.x * wpc + (threadIdx.x >> 5)) * 32ull * NB;
+    const unsigned long long W = static_cast<unsigned long long>(gridDim.x) * wpc;
+    const unsigned long long w = blockIdx.x * wpc + (threadIdx.x >> 5);
+    const unsigned long long U = (a.nblocks + 32ull * NB - 1) / (32ull * NB);
+    unsigned long long base, step, n;  // blocks base, base + step, ... below n
+    if (U <= kEvenSplitUnits * W) {
+        const unsigned long long u1 = (w + 1) * U / W;
+        base = w * U / W * 32ull * NB;
+        step = 32ull * NB;
+        n = u1 * 32ull * NB < a.nblocks ? u1 * 32ull * NB : a.nblocks;
+    } else {
+        base = w * 32ull * NB;
+        step = W * 32ull * NB;
+        n = a.nblocks;
+    }
 
     Tab<LAYOUT, DIR>::fill(smem, threadIdx.x, blockDim.x);
     __syncthreads();

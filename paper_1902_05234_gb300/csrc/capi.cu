@@ -92,10 +92,12 @@ uint32_t ecb_smem_bytes(int dir, const aes_launch_cfg &c) {
 }
 
 int validate_cfg(const aes_launch_cfg &c) {
-    if (c.blocks_per_thread != 1 && c.blocks_per_thread != 2 && c.blocks_per_thread != 4) return AES_E_CONFIG;
-    if (c.threads < 32 || c.threads % 32 || c.threads > max_threads_for_nb(c.blocks_per_thread))
+    if (c.blocks_per_thread != 1 && c.blocks_per_thread != 2 && c.blocks_per_thread != 4 &&
+        c.blocks_per_thread != 8)
         return AES_E_CONFIG;
-    if (c.layout < AES_LAYOUT_R4 || c.layout > AES_LAYOUT_R2) return AES_E_CONFIG;
+    if (c.layout < AES_LAYOUT_R4 || c.layout > AES_LAYOUT_REG) return AES_E_CONFIG;
+    if (c.threads < 32 || c.threads % 32 || c.threads > max_threads_for(c.blocks_per_thread, c.layout))
+        return AES_E_CONFIG;
     if (c.ctas_per_sm < 0 || c.ctas_per_sm > 32) return AES_E_CONFIG;
     return AES_OK;
 }

@@ -1,5 +1,5 @@
 // ecb_dec.cu -- instantiations of the ECB decryption kernel (Nr = 10/12/14;
-// 1, 2 or 4 blocks per thread; each table placement).
+// 1, 2, 4 or 8 blocks per thread; each table placement).
 #include "aes_kernels.cuh"
 #include "registry.h"
 
@@ -12,7 +12,9 @@ namespace aesgb {
     AESGB_K(NR, 1, kLayoutR4) AESGB_K(NR, 2, kLayoutR4) AESGB_K(NR, 4, kLayoutR4) \
     AESGB_K(NR, 1, kLayoutR1) AESGB_K(NR, 2, kLayoutR1) AESGB_K(NR, 4, kLayoutR1) \
     AESGB_K(NR, 1, kLayoutP4) AESGB_K(NR, 1, kLayoutConst) \
-    AESGB_K(NR, 1, kLayoutR2) AESGB_K(NR, 2, kLayoutR2) AESGB_K(NR, 4, kLayoutR2)
+    AESGB_K(NR, 1, kLayoutR2) AESGB_K(NR, 2, kLayoutR2) AESGB_K(NR, 4, kLayoutR2) \
+    AESGB_K(NR, 8, kLayoutR4) AESGB_K(NR, 8, kLayoutR2) \
+    AESGB_K(NR, 1, kLayoutReg) AESGB_K(NR, 2, kLayoutReg)
 
 AESGB_BOUNDS_READER(ecb_dec)
 

@@ -164,22 +164,22 @@ float time_launches(F launch, cudaStream_t s, int reps, int *status) {
 
 }  // namespace
 
-// Untuned choice: 2 blocks per thread and 1,024 threads when the buffer fills
-// every SM at least once over; smaller buffers get 1 block per thread and as
-// few threads per CTA as spread the work over all SMs.
+// Untuned choice: R4 tables, 2 blocks per thread and 1,024 threads when the
+// buffer fills every SM several times over; smaller buffers get R2 tables,
+// 1 block per thread and 512 threads at one CTA per SM, so that the next
+// launch's CTA fits beside this one and fills its tables while this one runs.
 aes_launch_cfg default_cfg(int /*dir*/, int /*nrounds*/, size_t nblocks) {
     aes_launch_cfg c;
-    c.layout = AES_LAYOUT_R4;
     c.ctas_per_sm = 1;
     const size_t sms = static_cast<size_t>(current_sms() > 0 ? current_sms() : 152);
-    if (nblocks >= sms * 2048) {
+    if (nblocks >= sms * 16384) {
+        c.layout = AES_LAYOUT_R4;
         c.threads = 1024;
         c.blocks_per_thread = 2;
         return c;
     }
-    size_t per_sm = (nblocks + sms - 1) / sms;
-    per_sm = (per_sm + 31) / 32 * 32;
-    c.threads = static_cast<int32_t>(per_sm < 128 ? 128 : (per_sm > 1024 ? 1024 : per_sm));
+    c.layout = AES_LAYOUT_R2;
+    c.threads = 512;
     c.blocks_per_thread = 1;
     return c;
 }
@@ -231,10 +231,16 @@ int aes_tune_ecb(int dir, int nrounds, const uint32_t *rk, const uint8_t *in, ui
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     std::vector<aes_launch_cfg> cands;
     for (int layout : {AES_LAYOUT_R4, AES_LAYOUT_R2, AES_LAYOUT_R1})
-        for (int nb : {1, 2, 4})
+        for (int nb : {1, 2, 4, 8})
             for (int th : {128, 256, 512, 768, 1024}) {
-                if (th > (nb >= 4 ? 512 : 1024)) continue;
+                if (th > (nb >= 8 ? 256 : nb >= 4 ? 512 : 1024)) continue;
+                if (nb == 8 && layout == AES_LAYOUT_R1) continue;  // not compiled
                 cands.push_back(aes_launch_cfg{th, nb, layout, 0});
+                // R2 encryption tables (64 KiB) at one CTA per SM leave room for
+                // the next launch's CTA, whose table fill then overlaps this
+                // launch (programmatic dependent launch): worth it at small sizes
+                if (layout == AES_LAYOUT_R2 && th >= 256 && th <= 512 && nb <= 4)
+                    cands.push_back(aes_launch_cfg{th, nb, layout, 1});
             }
     cands.push_back(default_cfg(dir, nrounds, nblocks));
     // enough launches that small sizes are timed over a few hundred

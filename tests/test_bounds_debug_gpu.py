@@ -60,11 +60,13 @@ def _report(aesgb, what):
 def _ecb_cfgs(aesgb):
     out = []
     for layout in (aesgb.LAYOUT_R4, aesgb.LAYOUT_R1, aesgb.LAYOUT_P4, aesgb.LAYOUT_CONST, aesgb.LAYOUT_R4_TMA,
-                   aesgb.LAYOUT_R2):
-        nbs = (1, 2, 4) if layout in (aesgb.LAYOUT_R4, aesgb.LAYOUT_R1, aesgb.LAYOUT_R4_TMA, aesgb.LAYOUT_R2) else (1,)
+                   aesgb.LAYOUT_R2, aesgb.LAYOUT_REG):
+        nbs = {aesgb.LAYOUT_R4: (1, 2, 4, 8), aesgb.LAYOUT_R2: (1, 2, 4, 8), aesgb.LAYOUT_R1: (1, 2, 4),
+               aesgb.LAYOUT_R4_TMA: (1, 2, 4), aesgb.LAYOUT_REG: (1, 2)}.get(layout, (1,))
         for nb in nbs:
-            for threads in (64, 512, 1024):
-                if nb == 4 and threads > 512:
+            for threads in (64, 256, 512, 1024):
+                limit = 256 if (nb == 8 or layout == aesgb.LAYOUT_REG) else 512 if nb == 4 else 1024
+                if threads > limit or (threads == 256 and limit > 256):
                     continue
                 for cps in (0, 1):
                     out.append(aesgb.make_cfg(threads, nb, layout, cps))

@@ -156,7 +156,7 @@ def test_default_cfg_is_valid():
     for d in (0, 1):
         for nr in (10, 12, 14):
             c = aesgb.aes_ecb_get_cfg(d, nr, 1 << 20)
-            assert c.threads % 32 == 0 and c.blocks_per_thread in (1, 2, 4)
+            assert c.threads % 32 == 0 and c.blocks_per_thread in (1, 2, 4, 8)
 
 
 def test_tune_cache_file_roundtrip(tmp_path):
@@ -177,8 +177,10 @@ def test_tune_cache_file_roundtrip(tmp_path):
         assert aesgb.aes_ecb_get_cfg(1, 12, 1 << 22).layout == aesgb.LAYOUT_R4
         aesgb.aes_tune_load(path)
         assert aesgb.aes_ecb_get_cfg(1, 12, 1 << 22).as_dict() == c.as_dict()
-        # a different size class is not affected
-        assert aesgb.aes_ecb_get_cfg(1, 12, 1 << 10).layout == aesgb.LAYOUT_R4
+        # a different size class is not affected: its default (small buffers: R2
+        # tables, one CTA of 512 threads per SM)
+        small = aesgb.aes_ecb_get_cfg(1, 12, 1 << 10)
+        assert small.layout == aesgb.LAYOUT_R2 and small.threads == 512 and small.ctas_per_sm == 1
         with pytest.raises(aesgb.AesError):
             aesgb.aes_tune_set_ecb(0, 10, 100, aesgb.make_cfg(threads=2048))
     finally:

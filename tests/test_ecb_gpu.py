@@ -45,18 +45,51 @@ def test_edge_sizes_default_cfg(orc, keybits, direction):
         assert np.array_equal(got, oracle_ecb(orc, direction, key, data)), f"n={n}"
 
 
+def test_default_cfg_both_sides_of_the_size_switch(orc):
+    """The untuned configuration switches from the small-buffer choice (R2
+    tables, one CTA of 512 threads per SM) to the large-buffer one (R4, 1,024
+    threads x 2 blocks) at 16,384 blocks per SM; the kernel itself switches
+    from even shares to grid-stride passes at 8 units per warp.  Buffers just
+    below and above the first switch, both directions, against the oracle."""
+    torch = torch_cuda()
+    sms = aesgb.aes_device_sm_count(torch.cuda.current_device())
+    key = wl.random_key(128, 12).tobytes()
+    for n in (sms * 16384 - 1, sms * 16384 + 33):
+        data = wl.random_bytes(16 * n, 13)
+        for direction in (0, 1):
+            cfg = aesgb.aes_ecb_get_cfg(direction, 10, n)
+            got, ok = gpu_ecb(direction, key, data, guard=64)
+            assert ok and np.array_equal(got, orc.ecb(direction, key, data, nthreads=16)), (n, direction, cfg)
+
+
 def all_cfgs():
     out = []
     for layout in (aesgb.LAYOUT_R4, aesgb.LAYOUT_R1, aesgb.LAYOUT_P4, aesgb.LAYOUT_CONST, aesgb.LAYOUT_R4_TMA,
-                   aesgb.LAYOUT_R2):
-        nbs = (1, 2, 4) if layout in (aesgb.LAYOUT_R4, aesgb.LAYOUT_R1, aesgb.LAYOUT_R4_TMA, aesgb.LAYOUT_R2) else (1,)
+                   aesgb.LAYOUT_R2, aesgb.LAYOUT_REG):
+        nbs = {aesgb.LAYOUT_R4: (1, 2, 4, 8), aesgb.LAYOUT_R2: (1, 2, 4, 8), aesgb.LAYOUT_R1: (1, 2, 4),
+               aesgb.LAYOUT_R4_TMA: (1, 2, 4), aesgb.LAYOUT_REG: (1, 2)}.get(layout, (1,))
         for nb in nbs:
             for threads in (64, 256, 512, 1024):
-                if nb == 4 and threads > 512:
+                limit = 256 if (nb == 8 or layout == aesgb.LAYOUT_REG) else 512 if nb == 4 else 1024
+                if threads > limit:
                     continue
                 for cps in (0, 1):
                     out.append(aesgb.make_cfg(threads, nb, layout, cps))
     return out
+
+
+def test_config_limits_refused():
+    """Configurations beyond a layout's compiled limits answer AES_E_CONFIG
+    before any launch: 128 B per thread above 256 threads or on the R1
+    layout, the register layout above 256 threads or at 64 B per thread."""
+    torch = torch_cuda()
+    enc, _, nr = aesgb.aes_expand_key(128, bytes(16))
+    x = torch.zeros(4096, dtype=torch.uint8, device="cuda")
+    for threads, nb, layout in ((512, 8, aesgb.LAYOUT_R4), (256, 8, aesgb.LAYOUT_R1), (512, 1, aesgb.LAYOUT_REG),
+                                (128, 4, aesgb.LAYOUT_REG), (256, 3, aesgb.LAYOUT_R4), (256, 1, 7)):
+        with pytest.raises(aesgb.AesError) as e:
+            aesgb.aes_ecb_crypt_cfg(0, enc, nr, x, x, 256, aesgb.make_cfg(threads, nb, layout, 0))
+        assert e.value.status == -12, (threads, nb, layout)
 
 
 @pytest.mark.parametrize("keybits", KEYBITS)
