@@ -74,6 +74,8 @@ def parse_args():
     p.add_argument("--study", action="store_true",
                    help="placement / granularity study (the paper's section 4 design axis) instead of the bench")
     p.add_argument("--study-reps", type=int, default=5, help="timed repetitions per study variant")
+    p.add_argument("--study-dir", type=int, choices=[0, 1], default=0,
+                   help="direction of the study's runs: 0 encrypt, 1 decrypt")
     p.add_argument("--study-warmup", type=int, default=2, help="warm-up repetitions per study variant")
     return p.parse_args()
 
@@ -698,9 +700,10 @@ STUDY_VARIANTS = [  # (label, layout, blocks/thread, threads)
 
 
 def run_study(args):
-    """Every table placement and granularity on one AES-128 encryption of
-    --bytes, each launched --study-warmup + --study-reps times (1 + 0 under ncu
-    gives one launch per variant, in the order listed)."""
+    """Every table placement and granularity on one AES-128 encryption (or,
+    with --study-dir 1, decryption) of --bytes, each launched --study-warmup +
+    --study-reps times (1 + 0 under ncu gives one launch per variant, in the
+    order listed)."""
     import torch
     from paper_1902_05234_gb300 import aesgb
     from paper_1902_05234_gb300 import workloads as wl
@@ -713,16 +716,18 @@ def run_study(args):
     x.random_(0, 256, generator=g)
     y = torch.empty_like(x)
     ref = torch.empty_like(x)
-    enc, _, nr = aesgb.aes_expand_key(128, wl.random_key(128, 100).tobytes())
+    enc, dec, nr = aesgb.aes_expand_key(128, wl.random_key(128, 100).tobytes())
+    d = args.study_dir
+    rk = enc if d == 0 else dec
     rows = []
     variants = STUDY_VARIANTS + [("constant time: bitsliced, no tables, 32 blocks per thread", None, 32, 256)]
     for i, (label, layout, nb, threads) in enumerate(variants):
         if layout is None:
             cfg = "aes_ecb_crypt_ct(threads=256, 32 blocks/thread)"
-            launch = lambda: aesgb.aes_ecb_crypt_ct(0, enc, nr, x, y, n)  # noqa: E731
+            launch = lambda: aesgb.aes_ecb_crypt_ct(d, rk, nr, x, y, n)  # noqa: E731
         else:
             cfg = aesgb.make_cfg(threads, nb, layout, 0)
-            launch = lambda c=cfg: aesgb.aes_ecb_crypt_cfg(0, enc, nr, x, y, n, c)  # noqa: E731
+            launch = lambda c=cfg: aesgb.aes_ecb_crypt_cfg(d, rk, nr, x, y, n, c)  # noqa: E731
         for _ in range(args.study_warmup):
             launch()
         ms = None
@@ -741,7 +746,8 @@ def run_study(args):
                      "ms": None if ms is None else round(ms, 4),
                      "gbps": None if ms is None else round(nbytes * 8 / ms / 1e6, 1),
                      "same_output": bool(torch.equal(y, ref))})
-    print(json.dumps({"study": "AES-128 ECB encryption, table placement x granularity",
+    print(json.dumps({"study": "AES-128 ECB " + ("encryption" if d == 0 else "decryption") +
+                      ", table placement x granularity",
                       "bytes": nbytes, "rows": rows}), flush=True)
 
 

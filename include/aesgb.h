@@ -244,6 +244,10 @@ typedef struct aes_batch_cfg {
     int32_t blocks_per_thread; /* 1, 2 or 4                                                           */
     int32_t chunk_passes;      /* a warp's unit of work = 32 * blocks_per_thread * chunk_passes blocks */
     int32_t ctas_per_sm;       /* 0 or 1 (the tables take most of the shared memory)                */
+    int32_t layout_enc;        /* table layout of the encryption phase and of the decryption      */
+    int32_t layout_dec;        /* phase (aes_layout; section 4.2): the pairs R4/R2 (the default,
+                                  blocks_per_thread 1, 2 or 4), R4/R4, R2/R2 and R1/R1 (1 or 2);
+                                  another pair is AES_E_CONFIG                                       */
 } aes_batch_cfg;
 
 /* Bytes of DEVICE workspace a batch of n descriptors needs (plan header, the
@@ -302,10 +306,19 @@ int aes_ecb_batch(const aes_desc *desc_dev, int n, void *stream);
  * loads the library, held until the process exits):
  *   n  at most AES_BATCH_NOALLOC_MAX_DESCS, else AES_E_RANGE (nothing queued).
  * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  Every call on a device uses the same array, so calls whose work
- * overlaps on the GPU (different streams without ordering) race and corrupt
- * each other: order them on one stream or synchronise between them. */
+ * device, with that device current) and sets the batch kernel's shared-memory
+ * limit; make that first call before any stream capture.  While another
+ * thread captures in global mode, call it on a stream created with
+ * cudaStreamNonBlocking: work on the legacy default stream (stream NULL) is
+ * refused then and invalidates that capture.  Every call on a device uses the
+ * same array, so calls whose work overlaps on the GPU (different streams
+ * without ordering) race and corrupt each other: order them on one stream or
+ * synchronise between them. */
+/* aes_ecb_batch with the optional per-message status array of
+ * aes_ecb_batch_ws (status_dev: DEVICE int32[n] or NULL), i.e. the library
+ * workspace per (device, stream) and the default or tuned configuration. */
+int aes_ecb_batch_ex(const aes_desc *desc_dev, int n, int32_t *status_dev, void *stream);
+
 #define AES_BATCH_NOALLOC_MAX_DESCS 16384
 int aes_ecb_batch_noalloc(const aes_desc *desc_dev, int n, int32_t *status_dev, void *stream);
 
@@ -476,6 +489,12 @@ int aes_srv_create(size_t mem_budget_bytes, int max_keys, int max_batch, int slo
  * naming key_id answer AES_E_BUSY.  AES_E_CUDA if the upload fails. */
 int aes_srv_put_key(aes_server *srv, int key_id, int keybits, const uint8_t *key);
 
+/* The same with the key already expanded: rk_enc and rk_dec (HOST,
+ * 4*(nrounds+1) words each, as aes_expand_key writes them), nrounds 10, 12 or
+ * 14 (AES_E_NROUNDS).  Same upload, refusal and ordering as aes_srv_put_key. */
+int aes_srv_put_schedule(aes_server *srv, int key_id, const uint32_t *rk_enc, const uint32_t *rk_dec,
+                         int nrounds);
+
 /* Submit one request arriving now: in_dev/out_dev DEVICE, 16-byte aligned,
  * equal or disjoint, nbytes a multiple of 16 with 2*nbytes <= budget
  * (AES_E_RANGE), key_id resident (AES_E_NOTFOUND; AES_E_BUSY while
@@ -541,8 +560,10 @@ int aes_srv_destroy(aes_server *srv);
  * them from then on.  If the environment variable AESGB_TUNE_CACHE names a
  * file, entries are loaded from it on first use and written to it after each
  * tuning run.  Tuning launches the kernels many times on the given buffers
- * (out is overwritten, in is only read), synchronises `stream` and takes
- * seconds. */
+ * (out is overwritten, in is only read): each candidate is captured in a CUDA
+ * graph of back-to-back launches on a stream of the tuner's own, which first
+ * waits for `stream`, and the replay is timed on the device.  The call
+ * synchronises that stream, makes `stream` wait for it and takes seconds. */
 
 /* Tune the single-buffer kernel for (dir, nrounds, size class of nblocks) on
  * the caller's DEVICE buffers (same rules as aes_ecb_crypt_cfg; rk HOST).
@@ -554,6 +575,14 @@ int aes_tune_ecb(int dir, int nrounds, const uint32_t *rk, const uint8_t *in, ui
  * aes_ecb_batch_ws without status; the batch is run many times). */
 int aes_tune_batch(const aes_desc *desc_dev, int n, void *ws, size_t ws_bytes, void *stream,
                    aes_batch_cfg *best);
+
+/* Tune the single-buffer kernel for (dir, nrounds, size class of
+ * bytes_hint / 16 blocks) without caller buffers: the call allocates an input
+ * and an output of bytes_hint bytes (stream-ordered on `stream`, released at
+ * the end; AES_E_NOMEM if they cannot be had) and runs aes_tune_ecb on them
+ * with an all-zero key (the kernels' time does not depend on key or data).
+ * AES_E_ARG for bytes_hint below 16. */
+int aes_tune(int dir, int nrounds, size_t bytes_hint, void *stream);
 
 /* Record a configuration by hand for (dir, nrounds, size class of nblocks). */
 int aes_tune_set_ecb(int dir, int nrounds, size_t nblocks, const aes_launch_cfg *cfg);

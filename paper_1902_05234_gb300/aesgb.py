@@ -59,11 +59,14 @@ class aes_desc(ctypes.Structure):
 
 class aes_batch_cfg(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("blocks_per_thread", ctypes.c_int32),
-                ("chunk_passes", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+                ("chunk_passes", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("layout_enc", ctypes.c_int32), ("layout_dec", ctypes.c_int32)]
 
     def __repr__(self):
         return (f"aes_batch_cfg(threads={self.threads}, bpt={16 * self.blocks_per_thread}B, "
-                f"chunk_passes={self.chunk_passes}, ctas_per_sm={self.ctas_per_sm})")
+                f"chunk_passes={self.chunk_passes}, ctas_per_sm={self.ctas_per_sm}, "
+                f"layouts={LAYOUT_NAMES.get(self.layout_enc, self.layout_enc)}/"
+                f"{LAYOUT_NAMES.get(self.layout_dec, self.layout_dec)})")
 
 
 class aes_srv_stats_t(ctypes.Structure):
@@ -105,6 +108,7 @@ _SIGNATURES = {
     "aes_batch_workspace_bytes": (_sz, [_i]),
     "aes_ecb_batch_ws": (_i, [_vp, _i, _vp, _sz, _vp, _vp, _vp]),
     "aes_ecb_batch": (_i, [_vp, _i, _vp]),
+    "aes_ecb_batch_ex": (_i, [_vp, _i, _vp, _vp]),
     "aes_ecb_batch_noalloc": (_i, [_vp, _i, _vp, _vp]),
     "aes_batch_graph_create": (_i, [_vp, _i, _vp, _sz, _vp, _vp, ctypes.POINTER(_vp)]),
     "aes_batch_graph_launch": (_i, [_vp, _vp]),
@@ -126,6 +130,7 @@ _SIGNATURES = {
     "aes_cbc_decrypt": (_i, [_u32p, _i, _u8p, _vp, _vp, _sz, _vp]),
     "aes_cfb_decrypt": (_i, [_u32p, _i, _u8p, _vp, _vp, _sz, _vp]),
     "aes_tune_ecb": (_i, [_i, _i, _u32p, _vp, _vp, _sz, _vp, ctypes.POINTER(aes_launch_cfg)]),
+    "aes_tune": (_i, [_i, _i, _sz, _vp]),
     "aes_tune_batch": (_i, [_vp, _i, _vp, _sz, _vp, ctypes.POINTER(aes_batch_cfg)]),
     "aes_tune_set_ecb": (_i, [_i, _i, _sz, ctypes.POINTER(aes_launch_cfg)]),
     "aes_batch_get_cfg": (_i, [_i, ctypes.POINTER(aes_batch_cfg)]),
@@ -134,6 +139,7 @@ _SIGNATURES = {
     "aes_tune_clear": (_i, []),
     "aes_srv_create": (_i, [_sz, _i, _i, _i, ctypes.POINTER(_vp)]),
     "aes_srv_put_key": (_i, [_vp, _i, _i, _u8p]),
+    "aes_srv_put_schedule": (_i, [_vp, _i, _u32p, _u32p, _i]),
     "aes_srv_submit": (_i, [_vp, _i, _i, _vp, _vp, _sz, ctypes.POINTER(ctypes.c_uint64)]),
     "aes_srv_submit_many": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "aes_srv_poll": (_i, [_vp, ctypes.c_uint64, ctypes.POINTER(_i), ctypes.POINTER(_i),
@@ -308,6 +314,10 @@ def aes_tune_ecb(direction: int, nrounds: int, rk, in_, out, nblocks: int, strea
     return c
 
 
+def aes_tune(direction: int, nrounds: int, bytes_hint: int, stream=None) -> None:
+    _check(lib().aes_tune(int(direction), int(nrounds), int(bytes_hint), _stream(stream)), "aes_tune")
+
+
 def aes_tune_batch(desc_dev, n: int, ws, ws_bytes: int, stream=None) -> aes_batch_cfg:
     c = aes_batch_cfg()
     _check(lib().aes_tune_batch(_ptr(desc_dev), int(n), _ptr(ws), int(ws_bytes), _stream(stream),
@@ -351,6 +361,12 @@ def aes_srv_put_key(srv: int, key_id: int, keybits: int, key) -> None:
     k = np.ascontiguousarray(np.frombuffer(bytes(key), np.uint8))
     _check(lib().aes_srv_put_key(_vp(srv), int(key_id), int(keybits), k.ctypes.data_as(_u8p)),
            "aes_srv_put_key")
+
+
+def aes_srv_put_schedule(srv: int, key_id: int, rk_enc, rk_dec, nrounds: int) -> None:
+    pe, _ke = _rk_arg(rk_enc)
+    pd, _kd = _rk_arg(rk_dec)
+    _check(lib().aes_srv_put_schedule(_vp(srv), int(key_id), pe, pd, int(nrounds)), "aes_srv_put_schedule")
 
 
 def aes_srv_submit(srv: int, key_id: int, direction: int, in_dev, out_dev, nbytes: int) -> int:
@@ -558,6 +574,10 @@ def aes_ecb_batch(desc_dev, n: int, stream=None) -> None:
     _check(lib().aes_ecb_batch(_ptr(desc_dev), int(n), _stream(stream)), "aes_ecb_batch")
 
 
+def aes_ecb_batch_ex(desc_dev, n: int, status_dev=None, stream=None) -> None:
+    _check(lib().aes_ecb_batch_ex(_ptr(desc_dev), int(n), _ptr(status_dev), _stream(stream)), "aes_ecb_batch_ex")
+
+
 def aes_ecb_batch_noalloc(desc_dev, n: int, status_dev=None, stream=None) -> None:
     """Batched ECB with the library's fixed device scratch (no allocation at
     all); at most AES_BATCH_NOALLOC_MAX_DESCS descriptors, calls must not
@@ -586,8 +606,10 @@ def aes_batch_graph_destroy(graph: int) -> None:
     _check(lib().aes_batch_graph_destroy(_vp(graph)), "aes_batch_graph_destroy")
 
 
-def make_batch_cfg(threads=512, blocks_per_thread=1, chunk_passes=32, ctas_per_sm=1) -> aes_batch_cfg:
-    return aes_batch_cfg(int(threads), int(blocks_per_thread), int(chunk_passes), int(ctas_per_sm))
+def make_batch_cfg(threads=512, blocks_per_thread=1, chunk_passes=32, ctas_per_sm=1, layout_enc=LAYOUT_R4,
+                   layout_dec=LAYOUT_R2) -> aes_batch_cfg:
+    return aes_batch_cfg(int(threads), int(blocks_per_thread), int(chunk_passes), int(ctas_per_sm),
+                         int(layout_enc), int(layout_dec))
 
 
 def pack_descs(rk, in_, out, nblocks, nrounds, direction) -> np.ndarray:

@@ -16,10 +16,12 @@
 //                    chunk).  A chunk's message is found by a warp-wide 32-ary
 //                    search in start[]; its round keys are staged through the
 //                    warp's own shared-memory slot into registers.  The CTA's T tables are filled for
-//                    encryption first (R4 layout, 128 KiB) and refilled once for
-//                    decryption (R2 layout, also 128 KiB: faster to fill than
-//                    R4's 160 KiB and as fast to use), between two CTA
-//                    barriers that every warp reaches.
+//                    encryption first and refilled once for decryption,
+//                    between two CTA barriers that every warp reaches; each
+//                    phase's table layout is part of the launch configuration
+//                    (default R4 for encryption, 128 KiB, and R2 for
+//                    decryption, also 128 KiB: faster to fill than R4's
+//                    160 KiB and as fast to use).
 //
 // Workspace layout (caller- or library-owned device memory, see
 // aes_batch_workspace_bytes):
@@ -222,10 +224,11 @@ struct BatchArgs {
 
 constexpr uint32_t kKeySlotBytes = 256;  // 60 words rounded up
 
-// Table layout of each direction's phase; both take 128 KiB.
-template <int DIR> constexpr int kBatchLayout = DIR == kEncrypt ? kLayoutR4 : kLayoutR2;
-constexpr uint32_t kBatchTableBytes = table_smem_bytes(kEncrypt, kLayoutR4);
-static_assert(table_smem_bytes(kDecrypt, kLayoutR2) == kBatchTableBytes, "both phases fit the same tables");
+// Shared memory of the tables of a launch: the larger of its two phases'.
+__host__ __device__ constexpr uint32_t batch_table_bytes(int le, int ld) {
+    return table_smem_bytes(kEncrypt, le) > table_smem_bytes(kDecrypt, ld) ? table_smem_bytes(kEncrypt, le)
+                                                                            : table_smem_bytes(kDecrypt, ld);
+}
 
 #if defined(AESGB_BOUNDS_CHECK)
 // Debug build: every chunk a warp takes adds one to its tag, so that after one
@@ -247,8 +250,8 @@ template <int NR> struct RegKey {
 // Blocks [first, first + count) of one message, as passes of 32*NB blocks per
 // warp with the next pass prefetched.  The round keys are read once per chunk
 // from the warp's shared-memory slot (16-byte broadcasts) into registers.
-template <int DIR, int NR, int NB>
-__device__ __forceinline__ void batch_chunk(const Tab<kBatchLayout<DIR>, DIR> &tab, const uint32_t *kslot,
+template <int DIR, int NR, int NB, int LAYOUT>
+__device__ __forceinline__ void batch_chunk(const Tab<LAYOUT, DIR> &tab, const uint32_t *kslot,
                                             const uint4 *in, uint4 *out, unsigned long long first,
                                             unsigned long long count, uint32_t lane) {
     RegKey<NR> key;
@@ -309,11 +312,11 @@ __device__ __forceinline__ int find_message(const unsigned long long *start, int
 // asks next (an atomic counter in the workspace; the next chunk index is
 // requested before the current chunk is processed, so the atomic's latency is
 // hidden).  Chunk c of this phase is chunk c_begin + c of the partition.
-template <int DIR, int NB>
+template <int DIR, int NB, int LAYOUT>
 __device__ void batch_phase(const BatchArgs &a, const WsView &v, uint8_t *smem, uint32_t *kslot,
                             unsigned long long c_begin, unsigned long long c_end) {
     const uint32_t lane = threadIdx.x & 31u;
-    const Tab<kBatchLayout<DIR>, DIR> tab(smem, lane);
+    const Tab<LAYOUT, DIR> tab(smem, lane);
     unsigned long long *counter = &v.hdr->next[DIR];
     const unsigned long long nchunks = c_end - c_begin;
     const unsigned int cb = v.hdr->chunk_blocks;
@@ -369,9 +372,9 @@ __device__ void batch_phase(const BatchArgs &a, const WsView &v, uint8_t *smem, 
         }
 #endif
         switch (nr) {
-        case 10: batch_chunk<DIR, 10, NB>(tab, kslot, in, out, first, cnt, lane); break;
-        case 12: batch_chunk<DIR, 12, NB>(tab, kslot, in, out, first, cnt, lane); break;
-        default: batch_chunk<DIR, 14, NB>(tab, kslot, in, out, first, cnt, lane); break;
+        case 10: batch_chunk<DIR, 10, NB, LAYOUT>(tab, kslot, in, out, first, cnt, lane); break;
+        case 12: batch_chunk<DIR, 12, NB, LAYOUT>(tab, kslot, in, out, first, cnt, lane); break;
+        default: batch_chunk<DIR, 14, NB, LAYOUT>(tab, kslot, in, out, first, cnt, lane); break;
         }
         rel = __shfl_sync(0xffffffffu, ticket, 0);
     }
@@ -379,38 +382,45 @@ __device__ void batch_phase(const BatchArgs &a, const WsView &v, uint8_t *smem, 
 
 constexpr int kBatchMaxThreads = 512;  // up to 128 registers: round keys live in registers
 
-template <int NB>
+// LE, LD: table layouts of the encryption and decryption phases.
+template <int NB, int LE, int LD>
 __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(const __grid_constant__ BatchArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     const WsView v = ws_view(a.ws, a.n);
     const unsigned long long T = v.hdr->total_chunks, E = v.hdr->enc_chunks;
-    uint32_t *kslot = reinterpret_cast<uint32_t *>(smem + kBatchTableBytes + (threadIdx.x >> 5) * kKeySlotBytes);
+    uint32_t *kslot =
+        reinterpret_cast<uint32_t *>(smem + batch_table_bytes(LE, LD) + (threadIdx.x >> 5) * kKeySlotBytes);
     if (E > 0) {
-        Tab<kBatchLayout<kEncrypt>, kEncrypt>::fill(smem, threadIdx.x, blockDim.x);
+        Tab<LE, kEncrypt>::fill(smem, threadIdx.x, blockDim.x);
         __syncthreads();
-        batch_phase<kEncrypt, NB>(a, v, smem, kslot, 0, E);
+        batch_phase<kEncrypt, NB, LE>(a, v, smem, kslot, 0, E);
     }
     if (T > E) {
         __syncthreads();  // every warp is done with the encryption tables
-        Tab<kBatchLayout<kDecrypt>, kDecrypt>::fill(smem, threadIdx.x, blockDim.x);
+        Tab<LD, kDecrypt>::fill(smem, threadIdx.x, blockDim.x);
         __syncthreads();
-        batch_phase<kDecrypt, NB>(a, v, smem, kslot, E, T);
+        batch_phase<kDecrypt, NB, LD>(a, v, smem, kslot, E, T);
     }
 }
 
 AESGB_BOUNDS_READER(batch)
 
-uint32_t batch_smem_bytes(int threads) {
-    return kBatchTableBytes + static_cast<uint32_t>(threads / 32) * kKeySlotBytes;
+uint32_t batch_smem_bytes(const aes_batch_cfg &c) {
+    return batch_table_bytes(c.layout_enc, c.layout_dec) + static_cast<uint32_t>(c.threads / 32) * kKeySlotBytes;
 }
 
-const void *batch_kernel_ptr(int nb) {
-    switch (nb) {
-    case 1: return reinterpret_cast<const void *>(&batch_kernel<1>);
-    case 2: return reinterpret_cast<const void *>(&batch_kernel<2>);
-    case 4: return reinterpret_cast<const void *>(&batch_kernel<4>);
-    default: return nullptr;
-    }
+// The compiled (blocks per thread, encryption layout, decryption layout)
+// combinations: the default pair R4 / R2 at 1, 2 and 4 blocks per thread, and
+// the pairs R4 / R4, R2 / R2 and R1 / R1 at 1 and 2 (the tuner's range).
+const void *batch_kernel_ptr(int nb, int le, int ld) {
+#define AESGB_BK(NB, LE, LD) \
+    if (nb == NB && le == LE && ld == LD) return reinterpret_cast<const void *>(&batch_kernel<NB, LE, LD>);
+    AESGB_BK(1, kLayoutR4, kLayoutR2) AESGB_BK(2, kLayoutR4, kLayoutR2) AESGB_BK(4, kLayoutR4, kLayoutR2)
+    AESGB_BK(1, kLayoutR4, kLayoutR4) AESGB_BK(2, kLayoutR4, kLayoutR4)
+    AESGB_BK(1, kLayoutR2, kLayoutR2) AESGB_BK(2, kLayoutR2, kLayoutR2)
+    AESGB_BK(1, kLayoutR1, kLayoutR1) AESGB_BK(2, kLayoutR1, kLayoutR1)
+#undef AESGB_BK
+    return nullptr;
 }
 
 int validate_batch_cfg(const aes_batch_cfg &c) {
@@ -418,6 +428,7 @@ int validate_batch_cfg(const aes_batch_cfg &c) {
     if (c.threads < 32 || c.threads % 32 || c.threads > kBatchMaxThreads) return AES_E_CONFIG;
     if (c.chunk_passes < 1 || c.chunk_passes > 1024) return AES_E_CONFIG;
     if (c.ctas_per_sm < 0 || c.ctas_per_sm > 1) return AES_E_CONFIG;
+    if (!batch_kernel_ptr(c.blocks_per_thread, c.layout_enc, c.layout_dec)) return AES_E_CONFIG;
     return AES_OK;
 }
 
@@ -436,8 +447,8 @@ int enqueue_batch(const aes_desc *desc, int n, void *ws, size_t ws_bytes, int32_
     batch_plan_kernel<<<1, kPlanThreads, 0, s>>>(desc, n, ws, status, chunk_blocks);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return AES_E_CUDA;
-    const void *fn = batch_kernel_ptr(c.blocks_per_thread);
-    const uint32_t smem = batch_smem_bytes(c.threads);
+    const void *fn = batch_kernel_ptr(c.blocks_per_thread, c.layout_enc, c.layout_dec);
+    const uint32_t smem = batch_smem_bytes(c);
     st = ensure_smem_attr(fn, dev, smem);
     if (st != AES_OK) return st;
     const int sms = sm_count(dev);
@@ -498,8 +509,8 @@ int enqueue_batch_kernel(const aes_desc *desc, int n, void *ws, const aes_batch_
     if (st != AES_OK) return st;
     int dev = 0;
     if (current_device(&dev) != AES_OK) return AES_E_CUDA;
-    const void *fn = batch_kernel_ptr(c.blocks_per_thread);
-    const uint32_t smem = batch_smem_bytes(c.threads);
+    const void *fn = batch_kernel_ptr(c.blocks_per_thread, c.layout_enc, c.layout_dec);
+    const uint32_t smem = batch_smem_bytes(c);
     st = ensure_smem_attr(fn, dev, smem);
     if (st != AES_OK) return st;
     const int sms = sm_count(dev);
@@ -587,7 +598,8 @@ int stream_workspace(int dev, cudaStream_t s, std::shared_ptr<StreamWs> *out) {
 
 // Enqueue the batch on s with the context's workspace, grown first if it is
 // smaller than `need` (w.mu held by the caller).
-int enqueue_with_stream_ws(StreamWs &w, const aes_desc *desc, int n, size_t need, cudaStream_t s) {
+int enqueue_with_stream_ws(StreamWs &w, const aes_desc *desc, int n, size_t need, int32_t *status,
+                           cudaStream_t s) {
     if (w.bytes < need) {
         const size_t sz = need < (1u << 20) ? (1u << 20) : need * 2;
         void *p = nullptr;
@@ -602,7 +614,7 @@ int enqueue_with_stream_ws(StreamWs &w, const aes_desc *desc, int n, size_t need
         w.last = nullptr;
         return AES_E_CUDA;
     }
-    const int st = enqueue_batch(desc, n, w.ptr, w.bytes, nullptr, batch_cfg_for(n), s);
+    const int st = enqueue_batch(desc, n, w.ptr, w.bytes, status, batch_cfg_for(n), s);
     if (st != AES_OK) return st;
     if (cudaEventRecord(w.last, s) != cudaSuccess) {
         (void)cudaGetLastError();
@@ -731,6 +743,10 @@ int aes_ecb_batch_ws(const aes_desc *desc_dev, int n, void *ws, size_t ws_bytes,
 }
 
 int aes_ecb_batch(const aes_desc *desc_dev, int n, void *stream) {
+    return aes_ecb_batch_ex(desc_dev, n, nullptr, stream);
+}
+
+int aes_ecb_batch_ex(const aes_desc *desc_dev, int n, int32_t *status_dev, void *stream) {
     if (n < 0) return AES_E_ARG;
     if (n == 0) return AES_OK;
     if (n > AES_BATCH_MAX_DESCS) return AES_E_RANGE;  // before the workspace is sized for it
@@ -750,7 +766,7 @@ int aes_ecb_batch(const aes_desc *desc_dev, int n, void *stream) {
     const int st = stream_workspace(dev, s, &w);
     if (st != AES_OK) return st;
     std::lock_guard<std::mutex> lk(w->mu);
-    return enqueue_with_stream_ws(*w, desc_dev, n, batch_ws_bytes(n), s);
+    return enqueue_with_stream_ws(*w, desc_dev, n, batch_ws_bytes(n), status_dev, s);
 }
 
 int aes_ecb_batch_noalloc(const aes_desc *desc_dev, int n, int32_t *status_dev, void *stream) {
@@ -781,7 +797,8 @@ int aes_batch_graph_create(const aes_desc *desc_dev, int n, void *ws, size_t ws_
     // one-time per-kernel set-up (shared-memory attribute) before capturing
     int dev = 0;
     if (current_device(&dev) != AES_OK) return AES_E_CUDA;
-    st0 = ensure_smem_attr(batch_kernel_ptr(c.blocks_per_thread), dev, batch_smem_bytes(c.threads));
+    st0 = ensure_smem_attr(batch_kernel_ptr(c.blocks_per_thread, c.layout_enc, c.layout_dec), dev,
+                           batch_smem_bytes(c));
     if (st0 != AES_OK) return st0;
     cudaStream_t s = nullptr;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return AES_E_CUDA;

@@ -77,8 +77,9 @@ struct Req {
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;        // after the batch kernel
-    cudaEvent_t ev_start = nullptr;  // before it: the stream has reached the batch
+    cudaEvent_t ev_start = nullptr;  // before it: the stream has reached the batch (unless it opened a period)
     uint64_t key_gen_seen = 0;       // key uploads this slot's stream has waited for
+    bool opened_period = false;      // the batch opened a busy period (it starts at Server::ref)
     // One page-locked buffer and its device copy per slot, uploaded with one
     // copy per batch: n descriptors at the start, the host-built plan (the
     // batch kernel's workspace) at the next 256-byte boundary.
@@ -236,7 +237,7 @@ void retire_locked(Server *s) {
         const bool ok = q == cudaSuccess;
         if (!ok) (void)cudaGetLastError();
         float a = 0.f, b = 0.f;
-        if (ok && cudaEventElapsedTime(&a, s->ref, sl.ev_start) == cudaSuccess &&
+        if (ok && (sl.opened_period || cudaEventElapsedTime(&a, s->ref, sl.ev_start) == cudaSuccess) &&
             cudaEventElapsedTime(&b, s->ref, sl.ev) == cudaSuccess) {
             s->period_iv.emplace_back(1e-3 * a, 1e-3 * b);
             s->timed_batches++;
@@ -323,6 +324,7 @@ bool pack_locked(Server *s, Launch *L) {
     L->n = n;
     L->blocks = blocks;
     L->new_period = busy == 0;
+    sl->opened_period = L->new_period;
     L->wait_keys = sl->key_gen_seen < s->key_gen;
     sl->key_gen_seen = s->key_gen;
     return true;
@@ -338,11 +340,12 @@ bool launch_unlocked(Server *s, const Launch &L, int sms) {
     const aes_batch_cfg cfg = serve_cfg(sms, L.blocks);
     const size_t ws_off = plan_offset(L.n);
     plan_on_host(sl->h_desc, L.n, batch_chunk_blocks(cfg), reinterpret_cast<uint8_t *>(sl->h_desc) + ws_off);
-    bool ok = !L.new_period || cudaEventRecord(s->ref, sl->stream) == cudaSuccess;
-    ok = ok && cudaMemcpyAsync(sl->d_desc, sl->h_desc, ws_off + batch_ws_bytes(L.n), cudaMemcpyHostToDevice,
-                               sl->stream) == cudaSuccess;
+    bool ok = cudaMemcpyAsync(sl->d_desc, sl->h_desc, ws_off + batch_ws_bytes(L.n), cudaMemcpyHostToDevice,
+                              sl->stream) == cudaSuccess;
     ok = ok && (!L.wait_keys || cudaStreamWaitEvent(sl->stream, s->key_ev, 0) == cudaSuccess);
-    ok = ok && cudaEventRecord(sl->ev_start, sl->stream) == cudaSuccess;
+    // the batch that opens a busy period starts at the period's reference
+    // event itself (interval start 0): one event record per launch fewer
+    ok = ok && cudaEventRecord(L.new_period ? s->ref : sl->ev_start, sl->stream) == cudaSuccess;
     ok = ok && enqueue_batch_kernel(sl->d_desc, L.n, reinterpret_cast<uint8_t *>(sl->d_desc) + ws_off, cfg,
                                     sl->stream) == AES_OK;
     ok = ok && cudaEventRecord(sl->ev, sl->stream) == cudaSuccess;
@@ -475,12 +478,8 @@ int aes_srv_create(size_t mem_budget_bytes, int max_keys, int max_batch, int slo
     return AES_OK;
 }
 
-int aes_srv_put_key(aes_server *h, int key_id, int keybits, const uint8_t *key) {
-    Server *s = as_server(h);
-    if (!s || key_id < 0 || key_id >= s->max_keys) return AES_E_ARG;
-    uint32_t enc[kRkStrideWords] = {0}, dec[kRkStrideWords] = {0};
-    const int nr = expand_key_host(keybits, key, enc, dec);
-    if (nr < 0) return nr;
+// Keep both schedules (HOST, kRkStrideWords words each) resident under key_id.
+static int put_schedules(Server *s, int key_id, const uint32_t *enc, const uint32_t *dec, int nr) {
     {
         std::lock_guard<std::mutex> lk(s->mu);
         // a queued or launched request would otherwise run with the new key
@@ -491,13 +490,12 @@ int aes_srv_put_key(aes_server *h, int key_id, int keybits, const uint8_t *key) 
     // pageable, so each copy returns once its bytes are staged; the event
     // orders the upload before the next batch of every slot.
     const size_t off = static_cast<size_t>(key_id) * kRkStrideWords;
+    const size_t bytes = kRkStrideWords * sizeof(uint32_t);
     int prev = 0;
     const bool have_prev = cudaGetDevice(&prev) == cudaSuccess;
     bool ok = cudaSetDevice(s->dev) == cudaSuccess &&
-              cudaMemcpyAsync(s->d_rk_enc + off, enc, sizeof enc, cudaMemcpyHostToDevice, s->key_stream) ==
-                  cudaSuccess &&
-              cudaMemcpyAsync(s->d_rk_dec + off, dec, sizeof dec, cudaMemcpyHostToDevice, s->key_stream) ==
-                  cudaSuccess &&
+              cudaMemcpyAsync(s->d_rk_enc + off, enc, bytes, cudaMemcpyHostToDevice, s->key_stream) == cudaSuccess &&
+              cudaMemcpyAsync(s->d_rk_dec + off, dec, bytes, cudaMemcpyHostToDevice, s->key_stream) == cudaSuccess &&
               cudaEventRecord(s->key_ev, s->key_stream) == cudaSuccess;
     if (!ok) (void)cudaGetLastError();
     if (have_prev) (void)cudaSetDevice(prev);
@@ -510,6 +508,26 @@ int aes_srv_put_key(aes_server *h, int key_id, int keybits, const uint8_t *key) 
         }
     }
     return ok ? AES_OK : AES_E_CUDA;
+}
+
+int aes_srv_put_key(aes_server *h, int key_id, int keybits, const uint8_t *key) {
+    Server *s = as_server(h);
+    if (!s || key_id < 0 || key_id >= s->max_keys) return AES_E_ARG;
+    uint32_t enc[kRkStrideWords] = {0}, dec[kRkStrideWords] = {0};
+    const int nr = expand_key_host(keybits, key, enc, dec);
+    if (nr < 0) return nr;
+    return put_schedules(s, key_id, enc, dec, nr);
+}
+
+int aes_srv_put_schedule(aes_server *h, int key_id, const uint32_t *rk_enc, const uint32_t *rk_dec, int nrounds) {
+    Server *s = as_server(h);
+    if (!s || key_id < 0 || key_id >= s->max_keys || !rk_enc || !rk_dec) return AES_E_ARG;
+    const int st = check_nrounds(nrounds);
+    if (st != AES_OK) return st;
+    uint32_t enc[kRkStrideWords] = {0}, dec[kRkStrideWords] = {0};
+    std::memcpy(enc, rk_enc, 16u * static_cast<unsigned>(nrounds + 1));
+    std::memcpy(dec, rk_dec, 16u * static_cast<unsigned>(nrounds + 1));
+    return put_schedules(s, key_id, enc, dec, nrounds);
 }
 
 static int submit_locked(Server *s, int key_id, int dir, const uint8_t *in, uint8_t *out, size_t nbytes,

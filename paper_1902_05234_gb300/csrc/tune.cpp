@@ -10,10 +10,12 @@
 // back after every tuning run.  The file is plain text, one entry per line
 // (lines of another format are ignored):
 //   ecb   <tag hex> <sms> <dir> <nr> <class> <threads> <blocks_per_thread> <layout> <ctas_per_sm>
-//   batch <tag hex> <sms> <threads> <blocks_per_thread> <chunk_passes> <ctas_per_sm>
+//   batch <tag hex> <sms> <threads> <blocks_per_thread> <chunk_passes> <ctas_per_sm> <layout_enc> <layout_dec>
+// (a batch line without the two layouts, as older files have, means R4 / R2)
 #include <cuda_runtime.h>
 
 #include <cstddef>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -102,8 +104,15 @@ int load_file_locked(const char *path) {
                         &a[6], &a[7]) == 9) {
             aes_launch_cfg c{a[4], a[5], a[6], a[7]};
             if (validate_cfg(c) == AES_OK) g_ecb[EcbKey{tag, a[0], a[1], a[2], a[3]}] = c;
-        } else if (std::sscanf(line, "batch %x %d %d %d %d %d", &tag, &a[0], &a[1], &a[2], &a[3], &a[4]) == 6) {
-            aes_batch_cfg c{a[1], a[2], a[3], a[4]};
+        } else {
+            const int got = std::sscanf(line, "batch %x %d %d %d %d %d %d %d", &tag, &a[0], &a[1], &a[2], &a[3], &a[4],
+                                        &a[5], &a[6]);
+            if (got != 6 && got != 8) continue;
+            if (got == 6) {
+                a[5] = AES_LAYOUT_R4;
+                a[6] = AES_LAYOUT_R2;
+            }
+            aes_batch_cfg c{a[1], a[2], a[3], a[4], a[5], a[6]};
             if (validate_batch_cfg(c) == AES_OK) g_batch[DevKey{tag, a[0]}] = c;
         }
     }
@@ -114,7 +123,7 @@ int load_file_locked(const char *path) {
 int save_file_locked(const char *path) {
     FILE *f = std::fopen(path, "w");
     if (!f) return AES_E_ARG;
-    std::fprintf(f, "# aesgb tune cache v2\n");
+    std::fprintf(f, "# aesgb tune cache v3\n");
     for (const auto &kv : g_ecb) {
         const auto &k = kv.first;
         const auto &c = kv.second;
@@ -123,8 +132,9 @@ int save_file_locked(const char *path) {
                      c.layout, c.ctas_per_sm);
     }
     for (const auto &kv : g_batch)
-        std::fprintf(f, "batch %08x %d %d %d %d %d\n", static_cast<unsigned int>(kv.first.first), kv.first.second,
-                     kv.second.threads, kv.second.blocks_per_thread, kv.second.chunk_passes, kv.second.ctas_per_sm);
+        std::fprintf(f, "batch %08x %d %d %d %d %d %d %d\n", static_cast<unsigned int>(kv.first.first),
+                     kv.first.second, kv.second.threads, kv.second.blocks_per_thread, kv.second.chunk_passes,
+                     kv.second.ctas_per_sm, kv.second.layout_enc, kv.second.layout_dec);
     const bool ok = std::fclose(f) == 0;
     return ok ? AES_OK : AES_E_ARG;
 }
@@ -141,23 +151,54 @@ void save_env_locked() {
     if (p && *p) (void)save_file_locked(p);
 }
 
-// Time `launch` (already validated) over `reps` launches after one warm-up.
+// Device time of one launch of `launch(stream)` (already validated): one
+// warm-up launch (it sets the kernel's attributes), then `reps` launches
+// captured in a CUDA graph on a private stream and the replay timed, so that
+// microsecond launches are timed back to back on the device as an
+// application's stream of launches runs them, not at the rate the host can
+// issue them.  The private stream first waits for the caller's stream `s`,
+// and `s` waits for it at the end.
 template <class F>
 float time_launches(F launch, cudaStream_t s, int reps, int *status) {
-    cudaEvent_t a = nullptr, b = nullptr;
-    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
-        *status = AES_E_CUDA;
-        return 0.f;
+    cudaStream_t ts = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr, join = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    int st = cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) == cudaSuccess &&
+                     cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess &&
+                     cudaEventCreateWithFlags(&join, cudaEventDisableTiming) == cudaSuccess
+                 ? AES_OK
+                 : AES_E_CUDA;
+    if (st == AES_OK)
+        st = cudaEventRecord(join, s) == cudaSuccess && cudaStreamWaitEvent(ts, join, 0) == cudaSuccess ? AES_OK
+                                                                                                     : AES_E_CUDA;
+    if (st == AES_OK) st = launch(ts);
+    if (st == AES_OK) st = cudaStreamBeginCapture(ts, cudaStreamCaptureModeThreadLocal) == cudaSuccess ? AES_OK
+                                                                                                       : AES_E_CUDA;
+    if (st == AES_OK) {
+        for (int r = 0; r < reps && st == AES_OK; ++r) st = launch(ts);
+        const bool ended = cudaStreamEndCapture(ts, &g) == cudaSuccess;
+        if (st == AES_OK && !ended) st = AES_E_CUDA;
     }
-    int st = launch();
-    if (st == AES_OK) st = cudaEventRecord(a, s) == cudaSuccess ? AES_OK : AES_E_CUDA;
-    for (int r = 0; r < reps && st == AES_OK; ++r) st = launch();
-    if (st == AES_OK) st = cudaEventRecord(b, s) == cudaSuccess ? AES_OK : AES_E_CUDA;
+    if (st == AES_OK) st = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess ? AES_OK : AES_E_CUDA;
+    if (st == AES_OK) st = cudaGraphLaunch(ge, ts) == cudaSuccess ? AES_OK : AES_E_CUDA;  // warm replay
+    if (st == AES_OK)
+        st = cudaEventRecord(a, ts) == cudaSuccess && cudaGraphLaunch(ge, ts) == cudaSuccess &&
+                     cudaEventRecord(b, ts) == cudaSuccess
+                 ? AES_OK
+                 : AES_E_CUDA;
     float ms = 0.f;
     if (st == AES_OK) st = cudaEventSynchronize(b) == cudaSuccess ? AES_OK : AES_E_CUDA;
     if (st == AES_OK) st = cudaEventElapsedTime(&ms, a, b) == cudaSuccess ? AES_OK : AES_E_CUDA;
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
+    if (st != AES_OK) (void)cudaGetLastError();
+    if (ts && join && cudaEventRecord(join, ts) == cudaSuccess) (void)cudaStreamWaitEvent(s, join, 0);
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    if (ts) cudaStreamDestroy(ts);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (join) cudaEventDestroy(join);
+    (void)cudaGetLastError();
     *status = st;
     return ms / static_cast<float>(reps);
 }
@@ -203,6 +244,8 @@ aes_batch_cfg default_batch_cfg() {
     c.blocks_per_thread = 1;
     c.chunk_passes = 32;
     c.ctas_per_sm = 1;
+    c.layout_enc = AES_LAYOUT_R4;
+    c.layout_dec = AES_LAYOUT_R2;
     return c;
 }
 
@@ -244,7 +287,7 @@ int aes_tune_ecb(int dir, int nrounds, const uint32_t *rk, const uint8_t *in, ui
             }
     cands.push_back(default_cfg(dir, nrounds, nblocks));
     // enough launches that small sizes are timed over a few hundred
-    // microseconds, and the better of two timings, so that launch-to-launch
+    // microseconds, and the better of two timings, so that replay-to-replay
     // noise does not pick a configuration at microsecond sizes
     const int reps = nblocks >= (size_t(1) << 24) ? 2 : (nblocks >= (size_t(1) << 18) ? 8 : 64);
     const int trials = nblocks >= (size_t(1) << 24) ? 1 : 2;
@@ -254,8 +297,9 @@ int aes_tune_ecb(int dir, int nrounds, const uint32_t *rk, const uint8_t *in, ui
         int tst = AES_OK;
         float ms = 1e30f;
         for (int t = 0; t < trials && tst == AES_OK; ++t) {
-            const float m = time_launches([&] { return launch_ecb(dir, rk, nrounds, in, out, nblocks, c, s); }, s,
-                                          reps, &tst);
+            const float m = time_launches(
+                [&](cudaStream_t ts) { return launch_ecb(dir, rk, nrounds, in, out, nblocks, c, ts); }, s, reps,
+                &tst);
             if (m < ms) ms = m;
         }
         if (tst != AES_OK) continue;  // e.g. a configuration that does not fit
@@ -281,20 +325,27 @@ int aes_tune_batch(const aes_desc *desc_dev, int n, void *ws, size_t ws_bytes, v
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     float best_ms = 1e30f;
     aes_batch_cfg best_cfg = default_batch_cfg();
+    auto consider = [&](const aes_batch_cfg &c) {
+        int tst = AES_OK;
+        const float ms = time_launches(
+            [&](cudaStream_t ts) { return aes_ecb_batch_ws(desc_dev, n, ws, ws_bytes, nullptr, &c, ts); }, s, 2,
+            &tst);
+        if (tst == AES_OK && ms < best_ms) {
+            best_ms = ms;
+            best_cfg = c;
+        }
+    };
+    // granularity and chunk size with the default table layouts, then the
+    // layout pairs (section 4.2's axis) at the best of those
     for (int nb : {1, 2})
         for (int th : {256, 384, 512})
-            for (int passes : {8, 16, 32, 64}) {
-                const aes_batch_cfg c{th, nb, passes, 1};
-                int tst = AES_OK;
-                const float ms = time_launches(
-                    [&] { return aes_ecb_batch_ws(desc_dev, n, ws, ws_bytes, nullptr, &c, stream); }, s, 2, &tst);
-                if (tst != AES_OK) continue;
-                if (ms < best_ms) {
-                    best_ms = ms;
-                    best_cfg = c;
-                }
-            }
+            for (int passes : {8, 16, 32, 64})
+                consider(aes_batch_cfg{th, nb, passes, 1, AES_LAYOUT_R4, AES_LAYOUT_R2});
     if (best_ms >= 1e29f) return AES_E_CUDA;
+    const aes_batch_cfg g = best_cfg;
+    const int pairs[][2] = {{AES_LAYOUT_R4, AES_LAYOUT_R4}, {AES_LAYOUT_R2, AES_LAYOUT_R2}, {AES_LAYOUT_R1, AES_LAYOUT_R1}};
+    for (const auto &p : pairs)
+        consider(aes_batch_cfg{g.threads, g.blocks_per_thread, g.chunk_passes, g.ctas_per_sm, p[0], p[1]});
     {
         std::lock_guard<std::mutex> lk(g_mu);
         load_env_locked();
@@ -303,6 +354,32 @@ int aes_tune_batch(const aes_desc *desc_dev, int n, void *ws, size_t ws_bytes, v
     }
     if (best) *best = best_cfg;
     return AES_OK;
+}
+
+int aes_tune(int dir, int nrounds, size_t bytes_hint, void *stream) {
+    if (dir != 0 && dir != 1) return AES_E_ARG;
+    int st = check_nrounds(nrounds);
+    if (st != AES_OK) return st;
+    const size_t nblocks = bytes_hint / 16;
+    if (nblocks == 0 || nblocks > (SIZE_MAX >> 5)) return AES_E_ARG;
+    // scratch input and output of the hinted size (stream-ordered); the
+    // kernels' time does not depend on the bytes, so neither is filled
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void *in = nullptr, *out = nullptr;
+    st = lib_malloc_device_async(&in, nblocks * 16, s);
+    if (st == AES_OK) st = lib_malloc_device_async(&out, nblocks * 16, s);
+    if (st == AES_OK) {
+        uint32_t enc[60] = {0}, dec[60] = {0};
+        const uint8_t key[32] = {0};
+        const int keybits = nrounds == 10 ? 128 : nrounds == 12 ? 192 : 256;
+        (void)expand_key_host(keybits, key, enc, dec);
+        st = aes_tune_ecb(dir, nrounds, dir == 0 ? enc : dec, static_cast<const uint8_t *>(in),
+                          static_cast<uint8_t *>(out), nblocks, stream, nullptr);
+    }
+    if (out) (void)cudaFreeAsync(out, s);
+    if (in) (void)cudaFreeAsync(in, s);
+    (void)cudaGetLastError();
+    return st;
 }
 
 int aes_tune_save(const char *path) {

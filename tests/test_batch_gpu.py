@@ -128,13 +128,37 @@ def test_batch_in_place(orc):
     check_against_oracle(orc, b, b.output())
 
 
+LAYOUT_PAIRS = [(aesgb.LAYOUT_R4, aesgb.LAYOUT_R2), (aesgb.LAYOUT_R4, aesgb.LAYOUT_R4),
+                (aesgb.LAYOUT_R2, aesgb.LAYOUT_R2), (aesgb.LAYOUT_R1, aesgb.LAYOUT_R1)]
+
+
 def batch_cfgs():
     out = []
     for nb in (1, 2, 4):
         for threads in (64, 256, 512):
             for passes in (1, 3, 8):
                 out.append(aesgb.make_batch_cfg(threads, nb, passes, 1))
+    for le, ld in LAYOUT_PAIRS[1:]:                  # the other table layouts of the two phases
+        for nb in (1, 2):
+            for threads in (64, 512):
+                for passes in (1, 8):
+                    out.append(aesgb.make_batch_cfg(threads, nb, passes, 1, le, ld))
     return out
+
+
+def test_batch_cfg_layout_pairs_refused_outside_the_compiled_set():
+    """A layout pair or granularity the batch kernel is not compiled for is
+    refused before any launch (AES_E_CONFIG)."""
+    torch = torch_cuda()
+    b = DeviceBatch(torch, [64, 4096], [128, 256], [0, 1], seed=10)
+    ws, nbytes = b.workspace()
+    for cfg in (aesgb.make_batch_cfg(512, 1, 8, 1, aesgb.LAYOUT_R2, aesgb.LAYOUT_R4),
+                aesgb.make_batch_cfg(512, 4, 8, 1, aesgb.LAYOUT_R2, aesgb.LAYOUT_R2),
+                aesgb.make_batch_cfg(512, 1, 8, 1, aesgb.LAYOUT_P4, aesgb.LAYOUT_P4),
+                aesgb.make_batch_cfg(512, 1, 8, 1, aesgb.LAYOUT_REG, aesgb.LAYOUT_REG)):
+        with pytest.raises(aesgb.AesError) as e:
+            aesgb.aes_ecb_batch_ws(b.desc_dev, b.n, ws, nbytes, cfg=cfg)
+        assert e.value.status == -12, repr(cfg)
 
 
 def test_batch_every_cfg(orc):
@@ -212,3 +236,25 @@ def test_batch_many_tiny_messages(orc):
     refh = ref.cpu().numpy()
     for i in range(0, n, 7):
         assert np.array_equal(b.message(got, i), b.message(refh, i)), i
+
+
+def test_library_workspace_batch_with_status(orc):
+    """aes_ecb_batch_ex: the library-owned workspace with the per-message
+    status array -- invalid descriptors are skipped with their status, every
+    other message equals the oracle."""
+    torch = torch_cuda()
+    lengths, keybits, dirs = small_mix(60, hi=32 * 1024, seed=12)
+    b = DeviceBatch(torch, lengths, keybits, dirs, seed=12)
+    b.table[5]["nrounds"] = 11
+    b.table[9]["dir"] = 3
+    b.upload()
+    status = torch.full((b.n,), 77, dtype=torch.int32, device="cuda")
+    aesgb.aes_ecb_batch_ex(b.desc_dev, b.n, status)
+    out = b.output()
+    st = status.cpu().numpy()
+    assert st[5] == -3 and st[9] == -1 and np.all(np.delete(st, [5, 9]) == 0)
+    for i in range(b.n):
+        if i in (5, 9):
+            assert np.all(b.message(out, i) == 0x5A), i
+        else:
+            assert np.array_equal(b.message(out, i), orc.ecb(int(b.dirs[i]), b.keys[i], b.message(b.data, i))), i

@@ -204,15 +204,16 @@ def run_batch(aesgb, orc):
     exp = np.concatenate([e for _, e in sorted(expected(b).items())])
     ws, nbytes = b.workspace()
     ncfg = 0
-    for nb in (1, 2, 4):
-        for threads in (64, 512):
-            for passes in (1, 5):
-                b.out_dev.fill_(0x5A)
-                cfg = aesgb.make_batch_cfg(threads, nb, passes, 1)
-                aesgb.aes_ecb_batch_ws(b.desc_dev, b.n, ws, nbytes, cfg=cfg)
-                tagged += check_coverage(n_chunks(b, cfg), ws)
-                assert np.array_equal(b.output(), exp), ("batch cfg", nb, threads, passes)
-                ncfg += 1
+    pairs = [(aesgb.LAYOUT_R4, aesgb.LAYOUT_R2, (1, 2, 4)), (aesgb.LAYOUT_R4, aesgb.LAYOUT_R4, (1, 2)),
+             (aesgb.LAYOUT_R2, aesgb.LAYOUT_R2, (1, 2)), (aesgb.LAYOUT_R1, aesgb.LAYOUT_R1, (1, 2))]
+    cfgs = [aesgb.make_batch_cfg(threads, nb, passes, 1, le, ld)
+            for le, ld, nbs in pairs for nb in nbs for threads in (64, 512) for passes in (1, 5)]
+    for cfg in cfgs:
+        b.out_dev.fill_(0x5A)
+        aesgb.aes_ecb_batch_ws(b.desc_dev, b.n, ws, nbytes, cfg=cfg)
+        tagged += check_coverage(n_chunks(b, cfg), ws)
+        assert np.array_equal(b.output(), exp), ("batch cfg", repr(cfg))
+        ncfg += 1
     default = n_chunks(b, aesgb.aes_batch_get_cfg(b.n))
     b.out_dev.fill_(0x5A)
     aesgb.aes_ecb_batch(b.desc_dev, b.n)

@@ -86,6 +86,14 @@ def test_argument_checks_before_cuda(lib):
     assert lib.aes_ecb_crypt_cfg(2, rk, 10, A, A + 4096, 4, ctypes.byref(aesgb.make_cfg()), None) == -1
 
 
+def test_tune_without_buffers_checks_arguments_first(lib):
+    """aes_tune refuses a bad direction, round count or size before it
+    allocates or touches a device."""
+    assert lib.aes_tune(2, 10, 1 << 20, None) == -1
+    assert lib.aes_tune(0, 11, 1 << 20, None) == -3
+    assert lib.aes_tune(0, 10, 8, None) == -1
+
+
 def test_debug_counter_is_debug_build_only(lib):
     """The release library has no index checks: its counter entry point
     answers AES_E_CONFIG (with a zero count) without touching the device."""
@@ -115,6 +123,7 @@ def test_batch_size_above_the_maximum_is_refused_before_any_work(lib):
     n = (1 << 28) + 1
     assert lib.aes_ecb_batch_ws(A, n, A, 1 << 40, None, None, None) == -10
     assert lib.aes_ecb_batch(A, n, None) == -10
+    assert lib.aes_ecb_batch_ex(A, n, None, None) == -10
     g = ctypes.c_void_p()
     assert lib.aes_batch_graph_create(A, n, A, 1 << 40, None, None, ctypes.byref(g)) == -10
     srv = ctypes.c_void_p()
@@ -122,6 +131,8 @@ def test_batch_size_above_the_maximum_is_refused_before_any_work(lib):
 
 
 def test_server_calls_reject_null_handle(lib):
+    rk = (ctypes.c_uint32 * 60)()
+    assert lib.aes_srv_put_schedule(None, 0, rk, rk, 10) == -1
     assert lib.aes_srv_cancel(None, 1) == -1
     assert lib.aes_srv_register(None, 1 << 20, 4096) == -1
     assert lib.aes_srv_unregister(None, 1 << 20) == -1

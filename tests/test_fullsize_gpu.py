@@ -232,13 +232,17 @@ def test_batch_every_tuner_candidate_fullsize():
     desc = torch.from_numpy(table.view(np.uint8).copy()).cuda()
     ws_bytes = aesgb.aes_batch_workspace_bytes(n)
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
-    for nb in (1, 2):
-        for th in (256, 384, 512):
-            for passes in (8, 16, 32, 64):
-                dst.fill_(0x5A)
-                aesgb.aes_ecb_batch_ws(desc, n, ws, ws_bytes, cfg=aesgb.make_batch_cfg(th, nb, passes, 1))
-                torch.cuda.synchronize()
-                assert torch.equal(dst, ref), (nb, th, passes)
+    pairs = [(aesgb.LAYOUT_R4, aesgb.LAYOUT_R2), (aesgb.LAYOUT_R4, aesgb.LAYOUT_R4),
+             (aesgb.LAYOUT_R2, aesgb.LAYOUT_R2), (aesgb.LAYOUT_R1, aesgb.LAYOUT_R1)]
+    for le, ld in pairs:                      # the tuner pairs each layout with the best of the rest
+        for nb in (1, 2):
+            for th in (256, 384, 512):
+                for passes in (8, 16, 32, 64):
+                    dst.fill_(0x5A)
+                    aesgb.aes_ecb_batch_ws(desc, n, ws, ws_bytes,
+                                           cfg=aesgb.make_batch_cfg(th, nb, passes, 1, le, ld))
+                    torch.cuda.synchronize()
+                    assert torch.equal(dst, ref), (le, ld, nb, th, passes)
 
 
 def _windows(nbytes, win, seed):

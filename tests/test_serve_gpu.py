@@ -228,6 +228,34 @@ def test_put_key_refused_while_a_request_names_it(orc):
         aesgb.aes_srv_destroy(srv)
 
 
+def test_put_schedule_keeps_expanded_keys(orc):
+    """aes_srv_put_schedule takes round keys already expanded (as
+    aes_expand_key writes them); requests under them equal the oracle.  A bad
+    round count is refused."""
+    torch = torch_cuda()
+    srv = aesgb.aes_srv_create(8 << 20, max_keys=3, max_batch=16, slots=2)
+    try:
+        keys = [wl.random_key(kb, 430 + i).tobytes() for i, kb in enumerate((128, 192, 256))]
+        for i, key in enumerate(keys):
+            enc, dec, nr = aesgb.aes_expand_key(8 * len(key), key)
+            aesgb.aes_srv_put_schedule(srv, i, enc, dec, nr)
+        with pytest.raises(aesgb.AesError) as e:
+            aesgb.aes_srv_put_schedule(srv, 0, enc, dec, 13)
+        assert e.value.status == -3
+        data = wl.random_bytes(3 * 8192, 433)
+        x = torch.from_numpy(data).cuda()
+        y = torch.full_like(x, 0x5A)
+        ts = [aesgb.aes_srv_submit(srv, i, i % 2, x[8192 * i:], y[8192 * i:], 8192) for i in range(3)]
+        for t in ts:
+            assert aesgb.aes_srv_wait(srv, t, 10000)[0] == 0
+        out = y.cpu().numpy()
+        for i in range(3):
+            w = slice(8192 * i, 8192 * (i + 1))
+            assert np.array_equal(out[w], orc.ecb(i % 2, keys[i], data[w])), i
+    finally:
+        aesgb.aes_srv_destroy(srv)
+
+
 def test_budget_caps_bytes_in_flight(orc, server):
     torch = torch_cuda()
     srv0, keys = server
