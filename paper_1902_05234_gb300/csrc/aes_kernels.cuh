@@ -63,6 +63,9 @@ struct EcbArgs {
     uint4 *out;
     unsigned long long nblocks;
     RoundKeys rk;
+    // At most this many units per warp take even contiguous shares (0: always
+    // grid-stride passes); see ecb_kernel.
+    unsigned int even_split_units;
 };
 
 __host__ __device__ constexpr uint32_t table_smem_bytes(int dir, int layout) {
@@ -410,15 +413,16 @@ __device__ __forceinline__ void st_block(uint4 *p, uint4 v) { __stcs(p, v); }
 // warp-wide 128-bit load/store covers 512 contiguous bytes; the next unit's
 // blocks are loaded before the current ones are ciphered.  Units are assigned
 // in one of two ways, decided per launch (the same in every warp):
-//  * at most kEvenSplitUnits units per warp (small buffers): warp w of W takes
-//    the contiguous units [w*U/W, (w+1)*U/W), so every SM gets the same work
-//    within one unit per warp and no launch ends on a partly filled pass;
+//  * at most a.even_split_units units per warp: warp w of W takes the
+//    contiguous units [w*U/W, (w+1)*U/W), so every CTA gets the same work
+//    within one unit per warp and no launch ends on a partly filled pass.  The
+//    host asks for it only when one CTA per SM is all that fits, so that every
+//    SM holds one CTA of the launch and the shares are per SM too;
 //  * otherwise grid-stride passes: warp w takes units w, w + W, w + 2W, ...,
 //    so the grid sweeps the buffer front to back (at most one pass of
-//    imbalance among hundreds).
+//    imbalance among many); with several CTAs per SM, CTAs that finish a pass
+//    early free their slots for the next launch's CTAs.
 // ---------------------------------------------------------------------------
-constexpr unsigned long long kEvenSplitUnits = 8;
-
 template <int DIR, int NR, int NB, int LAYOUT>
 __global__ void __launch_bounds__(max_threads_for(NB, LAYOUT), 1)
     ecb_kernel(const __grid_constant__ EcbArgs a) {
@@ -429,7 +433,7 @@ __global__ void __launch_bounds__(max_threads_for(NB, LAYOUT), 1)
     const unsigned long long w = blockIdx.x * wpc + (threadIdx.x >> 5);
     const unsigned long long U = (a.nblocks + 32ull * NB - 1) / (32ull * NB);
     unsigned long long base, step, n;  // blocks base, base + step, ... below n
-    if (U <= kEvenSplitUnits * W) {
+    if (U <= a.even_split_units * W) {
         const unsigned long long u1 = (w + 1) * U / W;
         base = w * U / W * 32ull * NB;
         step = 32ull * NB;

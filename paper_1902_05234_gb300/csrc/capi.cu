@@ -106,7 +106,7 @@ int validate_cfg(const aes_launch_cfg &c) {
 // more than the work needs.
 int persistent_grid(const void *fn, int dev, const aes_launch_cfg &c, uint32_t smem,
                     unsigned long long work_items_per_cta, unsigned long long total_items,
-                    int *grid) {
+                    int *grid, int *fit_per_sm) {
     const int sms = sm_count(dev);
     if (sms < 0) return sms;
     int fit = 0;
@@ -124,6 +124,7 @@ int persistent_grid(const void *fn, int dev, const aes_launch_cfg &c, uint32_t s
         g_occ[std::make_tuple(fn, dev, static_cast<int>(c.threads), smem)] = fit;
     }
     if (fit <= 0) return AES_E_CONFIG;
+    if (fit_per_sm) *fit_per_sm = fit;
     const int per_sm = c.ctas_per_sm > 0 && c.ctas_per_sm < fit ? c.ctas_per_sm : fit;
     const unsigned long long need = (total_items + work_items_per_cta - 1) / work_items_per_cta;
     unsigned long long g = static_cast<unsigned long long>(per_sm) * static_cast<unsigned long long>(sms);
@@ -159,15 +160,22 @@ int launch_ecb(int dir, const uint32_t *rk, int nr, const uint8_t *in, uint8_t *
     const uint32_t smem = ecb_smem_bytes(dir, c);
     int st = ensure_smem_attr(fn, dev, smem);
     if (st != AES_OK) return st;
-    int grid = 0;
+    int grid = 0, fit = 0;
     st = persistent_grid(fn, dev, c, smem,
-                         static_cast<unsigned long long>(c.threads) * c.blocks_per_thread, nblocks, &grid);
+                         static_cast<unsigned long long>(c.threads) * c.blocks_per_thread, nblocks, &grid, &fit);
     if (st != AES_OK) return st;
     EcbArgs args;
     args.in = reinterpret_cast<const uint4 *>(in);
     args.out = reinterpret_cast<uint4 *>(out);
     args.nblocks = nblocks;
     order_round_keys(dir, rk, nr, &args.rk);
+    // Even shares (up to 8 units per warp) only where a second CTA cannot fit
+    // beside the first: with room for two, the scheduler may place two CTAs
+    // of one launch on an SM, and fixed shares would then double that SM's
+    // work (4 MiB launches of one such configuration measured 5.4 and
+    // 3.1 Tbit/s in two runs), while grid-stride passes let CTAs that finish
+    // early free their slots.
+    args.even_split_units = fit == 1 ? 8u : 0u;
     uint32_t extra_tx = 0;  // the TMA-staged kernel's second parameter
     void *params[] = {&args, &extra_tx};
     return launch_pdl(fn, grid, c.threads, smem, params, stream);

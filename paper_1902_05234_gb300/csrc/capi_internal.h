@@ -29,8 +29,12 @@ int lib_malloc_device_async(void **p, size_t bytes, cudaStream_t s);
 int check_buffers(const void *in, const void *out, size_t nblocks);
 void order_round_keys(int dir, const uint32_t *rk, int nr, RoundKeys *out);
 int validate_cfg(const aes_launch_cfg &c);
+// Grid of a persistent launch: as many CTAs as fit (or c.ctas_per_sm) per SM,
+// never more than the work needs; *fit_per_sm (may be NULL) receives how many
+// CTAs of this kernel fit on one SM.
 int persistent_grid(const void *fn, int dev, const aes_launch_cfg &c, uint32_t smem,
-                    unsigned long long work_items_per_cta, unsigned long long total_items, int *grid);
+                    unsigned long long work_items_per_cta, unsigned long long total_items, int *grid,
+                    int *fit_per_sm);
 int launch_ecb(int dir, const uint32_t *rk, int nr, const uint8_t *in, uint8_t *out, size_t nblocks,
                const aes_launch_cfg &c, void *stream);
 

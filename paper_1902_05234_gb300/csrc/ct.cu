@@ -151,7 +151,8 @@ int aes_ecb_crypt_ct(int dir, const uint32_t *rk, int nrounds, const uint8_t *in
                               : reinterpret_cast<const void *>(&ct_kernel<1>);
     aes_launch_cfg c{kCtThreads, 1, 0, 0};
     int grid = 0;
-    st = persistent_grid(fn, dev, c, 0, static_cast<unsigned long long>(kCtThreads) * 32ull, nblocks, &grid);
+    st = persistent_grid(fn, dev, c, 0, static_cast<unsigned long long>(kCtThreads) * 32ull, nblocks, &grid,
+                         nullptr);
     if (st != AES_OK) return st;
     void *params[] = {&args};
     return launch_pdl(fn, grid, kCtThreads, 0, params, stream);

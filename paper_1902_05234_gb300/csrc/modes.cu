@@ -219,7 +219,7 @@ int launch_mode(const void *fn, int dir, const aes_launch_cfg &c, size_t nblocks
     if (st != AES_OK) return st;
     int grid = 0;
     st = persistent_grid(fn, dev, c, smem, static_cast<unsigned long long>(c.threads) * c.blocks_per_thread,
-                         nblocks, &grid);
+                         nblocks, &grid, nullptr);
     if (st != AES_OK) return st;
     void *params[] = {&args};
     return launch_pdl(fn, grid, c.threads, smem, params, stream);

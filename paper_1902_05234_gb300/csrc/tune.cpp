@@ -207,8 +207,9 @@ float time_launches(F launch, cudaStream_t s, int reps, int *status) {
 
 // Untuned choice: R4 tables, 2 blocks per thread and 1,024 threads when the
 // buffer fills every SM several times over; smaller buffers get R2 tables,
-// 1 block per thread and 512 threads at one CTA per SM, so that the next
-// launch's CTA fits beside this one and fills its tables while this one runs.
+// 2 blocks per thread and 256 threads with as many CTAs per SM as fit (three):
+// small CTAs spread a small buffer over every SM, and CTAs that finish early
+// make room for the next launch's CTAs to fill their tables.
 aes_launch_cfg default_cfg(int /*dir*/, int /*nrounds*/, size_t nblocks) {
     aes_launch_cfg c;
     c.ctas_per_sm = 1;
@@ -220,8 +221,9 @@ aes_launch_cfg default_cfg(int /*dir*/, int /*nrounds*/, size_t nblocks) {
         return c;
     }
     c.layout = AES_LAYOUT_R2;
-    c.threads = 512;
-    c.blocks_per_thread = 1;
+    c.threads = 256;
+    c.blocks_per_thread = 2;
+    c.ctas_per_sm = 0;
     return c;
 }
 
@@ -279,11 +281,6 @@ int aes_tune_ecb(int dir, int nrounds, const uint32_t *rk, const uint8_t *in, ui
                 if (th > (nb >= 8 ? 256 : nb >= 4 ? 512 : 1024)) continue;
                 if (nb == 8 && layout == AES_LAYOUT_R1) continue;  // not compiled
                 cands.push_back(aes_launch_cfg{th, nb, layout, 0});
-                // R2 encryption tables (64 KiB) at one CTA per SM leave room for
-                // the next launch's CTA, whose table fill then overlaps this
-                // launch (programmatic dependent launch): worth it at small sizes
-                if (layout == AES_LAYOUT_R2 && th >= 256 && th <= 512 && nb <= 4)
-                    cands.push_back(aes_launch_cfg{th, nb, layout, 1});
             }
     cands.push_back(default_cfg(dir, nrounds, nblocks));
     // enough launches that small sizes are timed over a few hundred

@@ -189,9 +189,10 @@ def test_tune_cache_file_roundtrip(tmp_path):
         aesgb.aes_tune_load(path)
         assert aesgb.aes_ecb_get_cfg(1, 12, 1 << 22).as_dict() == c.as_dict()
         # a different size class is not affected: its default (small buffers: R2
-        # tables, one CTA of 512 threads per SM)
+        # tables, 256 threads x 2 blocks, as many CTAs per SM as fit)
         small = aesgb.aes_ecb_get_cfg(1, 12, 1 << 10)
-        assert small.layout == aesgb.LAYOUT_R2 and small.threads == 512 and small.ctas_per_sm == 1
+        assert (small.layout, small.threads, small.blocks_per_thread, small.ctas_per_sm) == \
+            (aesgb.LAYOUT_R2, 256, 2, 0)
         with pytest.raises(aesgb.AesError):
             aesgb.aes_tune_set_ecb(0, 10, 100, aesgb.make_cfg(threads=2048))
     finally:

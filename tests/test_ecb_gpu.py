@@ -47,10 +47,10 @@ def test_edge_sizes_default_cfg(orc, keybits, direction):
 
 def test_default_cfg_both_sides_of_the_size_switch(orc):
     """The untuned configuration switches from the small-buffer choice (R2
-    tables, one CTA of 512 threads per SM) to the large-buffer one (R4, 1,024
-    threads x 2 blocks) at 16,384 blocks per SM; the kernel itself switches
-    from even shares to grid-stride passes at 8 units per warp.  Buffers just
-    below and above the first switch, both directions, against the oracle."""
+    tables, 256 threads x 2 blocks, three CTAs per SM) to the large-buffer one
+    (R4, 1,024 threads x 2 blocks, one CTA per SM) at 16,384 blocks per SM.
+    Buffers just below and above the switch, both directions, against the
+    oracle."""
     torch = torch_cuda()
     sms = aesgb.aes_device_sm_count(torch.cuda.current_device())
     key = wl.random_key(128, 12).tobytes()
@@ -307,3 +307,26 @@ def test_tma_wait_timeout_is_reported_and_context_survives(orc):
     assert aesgb.aes_wait_timeouts() == 0
     with pytest.raises(aesgb.AesError):
         aesgb.aes_tma_selftest_timeout(x, y, 65)
+
+
+@pytest.mark.parametrize("direction", [0, 1])
+def test_even_shares_at_one_cta_per_sm(orc, direction):
+    """With one CTA per SM (R4, 1,024 threads), up to 8 units (32 x blocks per
+    thread) per warp are split into even contiguous shares; above that the
+    kernel takes grid-stride passes.  Sizes around both ends of the even
+    range and ragged tails, against the oracle, in place and out of place."""
+    torch = torch_cuda()
+    sms = aesgb.aes_device_sm_count(torch.cuda.current_device())
+    key = wl.random_key(128, 14).tobytes()
+    warps = sms * 32
+    for nb in (1, 2):
+        cfg = aesgb.make_cfg(1024, nb, aesgb.LAYOUT_R4, 1)
+        unit = 32 * nb
+        for n in (1, unit * warps - 1, unit * warps + 17, 8 * unit * warps, 8 * unit * warps + 1,
+                  3 * unit * warps + 5):
+            data = wl.random_bytes(16 * n, 15 + n % 97)
+            exp = orc.ecb(direction, key, data, nthreads=16)
+            got, ok = gpu_ecb(direction, key, data, cfg=cfg, guard=64)
+            assert ok and np.array_equal(got, exp), (nb, n)
+            got, ok = gpu_ecb(direction, key, data, cfg=cfg, inplace=True, guard=64)
+            assert ok and np.array_equal(got, exp), (nb, n, "in place")
