@@ -610,6 +610,10 @@ def run_served(torch, aesgb, dev, n_req=20000, loads=(0.1, 0.2, 0.3, 0.4, 0.5, 0
                          "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 4),
                          "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 4),
                          "p99_queue_ms": round(float(np.percentile(queue, 99)) * 1e3, 4)})
+        # one more saturated pass with device timing on (off above: its events
+        # add about 10 us to a light-load request), for the batches' overlap
+        aesgb.aes_srv_set_device_timing(srv, True)
+        timed_gbps = total * 8 / run(None)[2] / 1e9
         stats = aesgb.aes_srv_stats(srv)
     finally:
         aesgb.aes_srv_destroy(srv)
@@ -621,6 +625,10 @@ def run_served(torch, aesgb, dev, n_req=20000, loads=(0.1, 0.2, 0.3, 0.4, 0.5, 0
            "submit_many_ms": round(statistics.median(submit_ms), 3),
            "identical_across_loads": identical, "batches_total": stats["batches"],
            "peak_inflight_bytes": stats["peak_inflight_bytes"],
+           "peak_busy_slots": stats["peak_busy_slots"],
+           "device_timing": {"peak_device_batches": stats["peak_device_batches"],
+                             "device_overlap_s": round(stats["device_overlap_s"], 4),
+                             "timed_batches": stats["timed_batches"], "saturated_gbps": round(timed_gbps, 1)},
            "loop_graph_gbps": loop["graph_gbps"], "loop_python_gbps": loop["python_gbps"],
            "speedup_vs_loop_graph": round(peak_bps * 8 / 1e9 / loop["graph_gbps"], 3),
            "speedup_vs_loop_python": round(peak_bps * 8 / 1e9 / loop["python_gbps"], 3),

@@ -446,9 +446,10 @@ int aes_ct_selftest_host(int dir, const uint32_t *rk, int nrounds, const uint8_t
  * validated at submission) and launches it on that slot's stream (descriptor
  * and plan upload, the persistent batch kernel, completion event).  Requests
  * that arrive while earlier batches run join the next batch; consecutive
- * batches overlap on the device.  A batch's device interval runs from the
- * moment its stream reaches the kernel (descriptors uploaded, two events
- * bound it) to the kernel's completion; aes_srv_stats reports how many such
+ * batches overlap on the device.  With device timing on
+ * (aes_srv_set_device_timing), a batch's device interval runs from the moment
+ * its stream reaches the kernel (descriptors uploaded; a timing event) to the
+ * kernel's completion (another); aes_srv_stats then reports how many such
  * intervals overlapped at most, and for how long.  The dispatcher holds the
  * server's lock only to pack and to retire batches, never across CUDA calls.
  * Host waits are bounded; nothing waits on the device.  Latency = host
@@ -466,7 +467,8 @@ typedef struct aes_srv_stats_t {
     uint64_t cancelled;     /* requests completed by aes_srv_cancel         */
     uint64_t peak_busy_slots;     /* most slots holding a launched, not yet
                                      retired batch at once (host view)       */
-    uint64_t timed_batches;       /* batches whose device interval was taken */
+    uint64_t timed_batches;       /* batches whose device interval was taken
+                                     (device timing on)                       */
     uint64_t peak_device_batches; /* most batches whose device intervals
                                      contain one instant                      */
     double device_overlap_s;      /* time in which two or more batches'
@@ -525,6 +527,15 @@ int aes_srv_results(aes_server *srv, int n, const uint64_t *tickets, int32_t *st
                     double *queue_s, int release);
 
 int aes_srv_stats(aes_server *srv, aes_srv_stats_t *out);
+
+/* Device timing of batches, off by default: on != 0 records two timing events
+ * per batch from the next busy period (the next launch that finds every slot
+ * idle) on, so that aes_srv_stats reports timed_batches, peak_device_batches
+ * and device_overlap_s; 0 stops it from the next busy period on.  The events
+ * add about 10 us to a light-load request's latency (measured on GB300), so
+ * leave it off where latency matters.  Host-side counters (peak_busy_slots,
+ * peak_inflight_bytes) are kept either way. */
+int aes_srv_set_device_timing(aes_server *srv, int on);
 
 /* Cancel a request that has not been launched yet (still queued: not arrived,
  * or waiting for budget or a slot).  It completes at once with status

@@ -140,6 +140,7 @@ _SIGNATURES = {
     "aes_srv_create": (_i, [_sz, _i, _i, _i, ctypes.POINTER(_vp)]),
     "aes_srv_put_key": (_i, [_vp, _i, _i, _u8p]),
     "aes_srv_put_schedule": (_i, [_vp, _i, _u32p, _u32p, _i]),
+    "aes_srv_set_device_timing": (_i, [_vp, _i]),
     "aes_srv_submit": (_i, [_vp, _i, _i, _vp, _vp, _sz, ctypes.POINTER(ctypes.c_uint64)]),
     "aes_srv_submit_many": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "aes_srv_poll": (_i, [_vp, ctypes.c_uint64, ctypes.POINTER(_i), ctypes.POINTER(_i),
@@ -367,6 +368,10 @@ def aes_srv_put_schedule(srv: int, key_id: int, rk_enc, rk_dec, nrounds: int) ->
     pe, _ke = _rk_arg(rk_enc)
     pd, _kd = _rk_arg(rk_dec)
     _check(lib().aes_srv_put_schedule(_vp(srv), int(key_id), pe, pd, int(nrounds)), "aes_srv_put_schedule")
+
+
+def aes_srv_set_device_timing(srv: int, on: bool) -> None:
+    _check(lib().aes_srv_set_device_timing(_vp(srv), 1 if on else 0), "aes_srv_set_device_timing")
 
 
 def aes_srv_submit(srv: int, key_id: int, direction: int, in_dev, out_dev, nbytes: int) -> int:

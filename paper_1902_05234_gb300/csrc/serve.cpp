@@ -21,10 +21,12 @@
 // outside it, so submissions and polls never wait behind CUDA calls.  Keys are
 // uploaded on a server-owned stream; a batch's stream waits for the newest
 // upload (an event) before its kernel.  A key that a queued or in-flight request
-// names cannot be replaced.  For each batch two events bound its device
-// interval: from the moment its stream reaches the kernel (descriptors
-// uploaded) to the kernel's completion; the intervals show how many batches
-// were on the device at once.
+// names cannot be replaced.  With device timing on (aes_srv_set_device_timing),
+// two timing events bound each batch's device interval: from the moment its
+// stream reaches the kernel (descriptors uploaded) to the kernel's completion;
+// the intervals show how many batches were on the device at once.  It is off
+// by default: timing events on a batch's stream added about 10 us to a
+// light-load request's latency, so the event the dispatcher polls never times.
 // Host waits are bounded (condition variables with timeouts); nothing on the
 // device waits.  Latency is host arrival -> host-observed completion.
 // Queued requests can be cancelled; an optional registry of device ranges
@@ -76,9 +78,11 @@ struct Req {
 
 struct Slot {
     cudaStream_t stream = nullptr;
-    cudaEvent_t ev = nullptr;        // after the batch kernel
-    cudaEvent_t ev_start = nullptr;  // before it: the stream has reached the batch (unless it opened a period)
+    cudaEvent_t ev = nullptr;        // after the batch kernel (no timing: the dispatcher polls it)
+    cudaEvent_t t_start = nullptr;   // device timing: the stream has reached the batch (unless it opened a period)
+    cudaEvent_t t_end = nullptr;     // device timing: the batch kernel has completed
     uint64_t key_gen_seen = 0;       // key uploads this slot's stream has waited for
+    bool timed = false;              // the batch carries the two timing events
     bool opened_period = false;      // the batch opened a busy period (it starts at Server::ref)
     // One page-locked buffer and its device copy per slot, uploaded with one
     // copy per batch: n descriptors at the start, the host-built plan (the
@@ -132,6 +136,8 @@ struct Server {
     // launch that found every slot idle until all are retired again), in
     // seconds after `ref`, an event recorded at the period's first launch.
     cudaEvent_t ref = nullptr;
+    bool device_timing = false;  // aes_srv_set_device_timing
+    bool period_timed = false;   // the current busy period was opened by a timed batch
     std::vector<std::pair<double, double>> period_iv;
     uint64_t timed_batches = 0, peak_dev = 0;
     double overlap_s = 0;
@@ -175,7 +181,8 @@ void free_server(Server *s) {
     for (Slot &sl : s->slots) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);
         if (sl.ev) cudaEventDestroy(sl.ev);
-        if (sl.ev_start) cudaEventDestroy(sl.ev_start);
+        if (sl.t_start) cudaEventDestroy(sl.t_start);
+        if (sl.t_end) cudaEventDestroy(sl.t_end);
         if (sl.stream) cudaStreamDestroy(sl.stream);
         if (sl.h_desc) cudaFreeHost(sl.h_desc);
         if (sl.d_desc) cudaFree(sl.d_desc);
@@ -237,8 +244,9 @@ void retire_locked(Server *s) {
         const bool ok = q == cudaSuccess;
         if (!ok) (void)cudaGetLastError();
         float a = 0.f, b = 0.f;
-        if (ok && (sl.opened_period || cudaEventElapsedTime(&a, s->ref, sl.ev_start) == cudaSuccess) &&
-            cudaEventElapsedTime(&b, s->ref, sl.ev) == cudaSuccess) {
+        if (ok && sl.timed &&
+            (sl.opened_period || cudaEventElapsedTime(&a, s->ref, sl.t_start) == cudaSuccess) &&
+            cudaEventElapsedTime(&b, s->ref, sl.t_end) == cudaSuccess) {
             s->period_iv.emplace_back(1e-3 * a, 1e-3 * b);
             s->timed_batches++;
         }
@@ -268,6 +276,7 @@ struct Launch {
     int n = 0;
     unsigned long long blocks = 0;
     bool new_period = false;  // every other slot was idle: the batch opens a busy period
+    bool timed = false;       // record the batch's device interval
     bool wait_keys = false;   // keys were uploaded since this slot's stream last waited
 };
 
@@ -324,7 +333,11 @@ bool pack_locked(Server *s, Launch *L) {
     L->n = n;
     L->blocks = blocks;
     L->new_period = busy == 0;
+    // a period is timed as a whole: only if timing was on when it opened
+    if (L->new_period) s->period_timed = s->device_timing;
+    L->timed = s->period_timed;
     sl->opened_period = L->new_period;
+    sl->timed = L->timed;
     L->wait_keys = sl->key_gen_seen < s->key_gen;
     sl->key_gen_seen = s->key_gen;
     return true;
@@ -345,9 +358,10 @@ bool launch_unlocked(Server *s, const Launch &L, int sms) {
     ok = ok && (!L.wait_keys || cudaStreamWaitEvent(sl->stream, s->key_ev, 0) == cudaSuccess);
     // the batch that opens a busy period starts at the period's reference
     // event itself (interval start 0): one event record per launch fewer
-    ok = ok && cudaEventRecord(L.new_period ? s->ref : sl->ev_start, sl->stream) == cudaSuccess;
+    ok = ok && (!L.timed || cudaEventRecord(L.new_period ? s->ref : sl->t_start, sl->stream) == cudaSuccess);
     ok = ok && enqueue_batch_kernel(sl->d_desc, L.n, reinterpret_cast<uint8_t *>(sl->d_desc) + ws_off, cfg,
                                     sl->stream) == AES_OK;
+    ok = ok && (!L.timed || cudaEventRecord(sl->t_end, sl->stream) == cudaSuccess);
     ok = ok && cudaEventRecord(sl->ev, sl->stream) == cudaSuccess;
     if (!ok) (void)cudaGetLastError();
     return ok;
@@ -460,7 +474,8 @@ int aes_srv_create(size_t mem_budget_bytes, int max_keys, int max_batch, int slo
         sl.buf_bytes = plan_offset(max_batch) + aes_batch_workspace_bytes(max_batch);
         void *hb = nullptr, *db = nullptr;
         ok = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) == cudaSuccess &&
-             cudaEventCreate(&sl.ev) == cudaSuccess && cudaEventCreate(&sl.ev_start) == cudaSuccess;
+             cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreate(&sl.t_start) == cudaSuccess && cudaEventCreate(&sl.t_end) == cudaSuccess;
         if (!ok) st = AES_E_CUDA;
         ok = ok && (st = lib_malloc_host(&hb, sl.buf_bytes)) == AES_OK &&
              (st = lib_malloc_device(&db, sl.buf_bytes)) == AES_OK;
@@ -716,6 +731,14 @@ int aes_srv_unregister(aes_server *h, const void *base_dev) {
     if (!s || !base_dev) return AES_E_ARG;
     std::lock_guard<std::mutex> lk(s->mu);
     return s->regs.erase(reinterpret_cast<uintptr_t>(base_dev)) ? AES_OK : AES_E_NOTFOUND;
+}
+
+int aes_srv_set_device_timing(aes_server *h, int on) {
+    Server *s = as_server(h);
+    if (!s) return AES_E_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->device_timing = on != 0;
+    return AES_OK;
 }
 
 int aes_srv_stats(aes_server *h, aes_srv_stats_t *out) {

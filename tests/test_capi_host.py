@@ -133,6 +133,7 @@ def test_batch_size_above_the_maximum_is_refused_before_any_work(lib):
 def test_server_calls_reject_null_handle(lib):
     rk = (ctypes.c_uint32 * 60)()
     assert lib.aes_srv_put_schedule(None, 0, rk, rk, 10) == -1
+    assert lib.aes_srv_set_device_timing(None, 1) == -1
     assert lib.aes_srv_cancel(None, 1) == -1
     assert lib.aes_srv_register(None, 1 << 20, 4096) == -1
     assert lib.aes_srv_unregister(None, 1 << 20) == -1

@@ -150,6 +150,7 @@ def test_batches_overlap_on_the_device(orc):
         keys = {k: wl.random_key((256, 128, 192, 256)[k], 410 + k).tobytes() for k in range(4)}
         for k in range(4):
             aesgb.aes_srv_put_key(srv, k, 8 * len(keys[k]), keys[k])
+        aesgb.aes_srv_set_device_timing(srv, True)
         big_n = 1 << 30
         gen = torch.Generator(device="cuda").manual_seed(190205230 + 411)
         big_in = torch.randint(0, 256, (big_n,), dtype=torch.uint8, device="cuda", generator=gen)
@@ -194,6 +195,30 @@ def test_batches_overlap_on_the_device(orc):
         alone_h = alone.cpu().numpy()
         for i in range(0, m, 9):
             assert np.array_equal(a.msg(alone_h, i), a.msg(out, i)), i
+    finally:
+        aesgb.aes_srv_destroy(srv)
+
+
+def test_device_timing_is_off_by_default():
+    """Without aes_srv_set_device_timing no batch carries timing events (no
+    device intervals), while the host-side counters are kept; switched on, the
+    next busy period's batches are timed."""
+    torch = torch_cuda()
+    srv = aesgb.aes_srv_create(8 << 20, max_keys=1, max_batch=16, slots=2)
+    try:
+        aesgb.aes_srv_put_key(srv, 0, 128, bytes(16))
+        x = torch.zeros(1 << 16, dtype=torch.uint8, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(3):
+            aesgb.aes_srv_wait(srv, aesgb.aes_srv_submit(srv, 0, 0, x, y, x.numel()), 10000)
+        st = aesgb.aes_srv_stats(srv)
+        assert st["batches"] == 3 and st["timed_batches"] == 0 and st["peak_busy_slots"] >= 1
+        assert st["peak_device_batches"] == 0 and st["device_overlap_s"] == 0.0
+        aesgb.aes_srv_set_device_timing(srv, True)
+        for _ in range(2):
+            aesgb.aes_srv_wait(srv, aesgb.aes_srv_submit(srv, 0, 0, x, y, x.numel()), 10000)
+        st = aesgb.aes_srv_stats(srv)
+        assert st["batches"] == 5 and st["timed_batches"] == 2 and st["peak_device_batches"] >= 1
     finally:
         aesgb.aes_srv_destroy(srv)
 
