@@ -28,6 +28,7 @@
 //   BatchHeader | uint32 order[n] | uint64 start[n+1] | uint64 count[n]
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <map>
@@ -544,6 +545,7 @@ struct StreamWs {
     size_t bytes = 0;
     int dev = 0;
     cudaEvent_t last = nullptr;  // recorded after the newest batch that uses ptr
+    std::atomic<int> users{0};   // callers that looked it up and have not finished (never evicted then)
 };
 using WsKey = std::pair<int, unsigned long long>;  // device, stream id
 std::mutex g_ws_mu;
@@ -559,7 +561,7 @@ void evict_idle_locked(const StreamWs *keep, cudaStream_t s) {
     for (auto it = g_ws.begin(); it != g_ws.end() && g_ws.size() > kMaxStreamWs;) {
         StreamWs &w = *it->second;
         std::unique_lock<std::mutex> lk(w.mu, std::try_to_lock);
-        const bool idle = &w != keep && lk.owns_lock() &&
+        const bool idle = &w != keep && w.users.load() == 0 && lk.owns_lock() &&
                           (w.last == nullptr || cudaEventQuery(w.last) == cudaSuccess);
         (void)cudaGetLastError();
         if (!idle) {
@@ -578,7 +580,9 @@ void evict_idle_locked(const StreamWs *keep, cudaStream_t s) {
 }
 }  // namespace
 
-// The context of (dev, stream s), created on first use.
+// The context of (dev, stream s), created on first use.  Its user count is
+// raised here, under the map's mutex, so eviction (also under it) never takes
+// a context that a caller is about to lock; the caller lowers it when done.
 int stream_workspace(int dev, cudaStream_t s, std::shared_ptr<StreamWs> *out) {
     unsigned long long id = 0;
     if (cudaStreamGetId(s, &id) != cudaSuccess) {
@@ -592,6 +596,7 @@ int stream_workspace(int dev, cudaStream_t s, std::shared_ptr<StreamWs> *out) {
         slot->dev = dev;
     }
     *out = slot;  // (evict_idle_locked keeps this entry, so the reference stays valid)
+    (*out)->users.fetch_add(1);
     if (g_ws.size() > kMaxStreamWs) evict_idle_locked(out->get(), s);
     return AES_OK;
 }
@@ -765,8 +770,13 @@ int aes_ecb_batch_ex(const aes_desc *desc_dev, int n, int32_t *status_dev, void 
     std::shared_ptr<StreamWs> w;
     const int st = stream_workspace(dev, s, &w);
     if (st != AES_OK) return st;
-    std::lock_guard<std::mutex> lk(w->mu);
-    return enqueue_with_stream_ws(*w, desc_dev, n, batch_ws_bytes(n), status_dev, s);
+    int r;
+    {
+        std::lock_guard<std::mutex> lk(w->mu);
+        r = enqueue_with_stream_ws(*w, desc_dev, n, batch_ws_bytes(n), status_dev, s);
+    }
+    w->users.fetch_sub(1);
+    return r;
 }
 
 int aes_ecb_batch_noalloc(const aes_desc *desc_dev, int n, int32_t *status_dev, void *stream) {

@@ -206,3 +206,26 @@ def test_library_workspace_batch_refuses_a_capturing_stream(orc):
     g.replay()
     torch.cuda.synchronize()
     _check_pooled(orc, b, b["y"].cpu().numpy())
+
+
+def test_library_workspaces_of_many_streams(orc):
+    """More than 64 streams each run a batch through the library workspace:
+    once 64 per-stream workspaces exist, the idle ones of other streams are
+    released as new streams arrive.  Every stream's output stays exact, and
+    reusing an early stream (its workspace released) allocates a new one."""
+    torch = torch_cuda()
+    aesgb.aes_shutdown()
+    b = _pooled_batch(torch, 40, 1 << 10, 795)
+    streams = [torch.cuda.Stream() for _ in range(80)]
+    for s in streams:
+        b["y"].fill_(0x5A)
+        torch.cuda.synchronize()
+        aesgb.aes_ecb_batch(b["desc"], b["n"], s)
+        s.synchronize()
+        _check_pooled(orc, b, b["y"].cpu().numpy())
+    b["y"].fill_(0x5A)
+    torch.cuda.synchronize()
+    aesgb.aes_ecb_batch(b["desc"], b["n"], streams[0])
+    streams[0].synchronize()
+    _check_pooled(orc, b, b["y"].cpu().numpy())
+    aesgb.aes_shutdown()
