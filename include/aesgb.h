@@ -30,15 +30,18 @@
  *    the kernel's shared-memory limit and caches its occupancy (host calls,
  *    not stream work).  Make one call of each configuration before capturing
  *    the enqueuing calls into a graph; after that they only enqueue kernels.
- *    aes_batch_graph_create does this set-up itself.
+ *    aes_batch_graph_create does this set-up itself.  aes_ecb_batch and
+ *    aes_ecb_batch_ex refuse a capturing stream (their workspace belongs to
+ *    the library); capture aes_ecb_batch_ws instead.
  *  - Launch overlap: the single-buffer kernels are launched with
  *    programmatic stream serialisation, so one may start (fill its tables)
  *    while the previous kernel in the stream drains; it waits for that
  *    kernel to complete before touching global memory, so stream order
  *    semantics are unchanged.
  *  - Thread safety: calls may come from several host threads on distinct
- *    streams; library state (caches, tuned configurations, internal streams)
- *    is guarded.  A server handle is the exception (see aes_srv_create).
+ *    streams; library state (caches, tuned configurations, internal streams,
+ *    the per-stream batch workspaces) is guarded.  A server handle is the
+ *    exception (see aes_srv_create).
  */
 #ifndef AESGB_H
 #define AESGB_H
