@@ -163,10 +163,12 @@ def test_stress_16gib_aes256_decrypt_in_place(orc):
 def _tuner_candidates():
     """The configurations aes_tune_ecb chooses among (tune.cpp)."""
     out = []
-    for layout in (aesgb.LAYOUT_R4, aesgb.LAYOUT_R1):
-        for nb in (1, 2, 4):
+    for layout in (aesgb.LAYOUT_R4, aesgb.LAYOUT_R2, aesgb.LAYOUT_R1):
+        for nb in (1, 2, 4, 8):
             for th in (128, 256, 512, 768, 1024):
-                if th > (512 if nb >= 4 else 1024):
+                if th > (256 if nb >= 8 else 512 if nb >= 4 else 1024):
+                    continue
+                if nb == 8 and layout == aesgb.LAYOUT_R1:
                     continue
                 out.append(aesgb.make_cfg(th, nb, layout, 0))
     out.append(aesgb.aes_ecb_get_cfg(0, 10, (1 << 30) // 16))
