@@ -22,8 +22,9 @@ checked against the oracle, properties over the whole buffer on the device.
 * the largest single call: 2^32 + 1 blocks (64 GiB + 16 B) in place, windows
   around block 2^32 against the oracle and back.
 * 1 GiB through the other kernels the benchmark times: the constant-time
-  kernel (every key size), the TMA-staged layout, CTR, CBC and CFB decryption --
-  oracle windows, and round trips over the whole buffer.
+  kernel (every key size), the TMA-staged layout, the R2 layout, the table in
+  registers and 128 B per thread, CTR, CBC and CFB decryption -- oracle
+  windows, and round trips over the whole buffer.
 """
 import numpy as np
 import pytest
@@ -317,6 +318,36 @@ def test_1gib_r2_layout_windows_and_roundtrip(orc, keybits, cfg):
     torch.cuda.synchronize()
     win = 64 * 1024
     for s in _windows(nbytes, win, 75):
+        assert np.array_equal(y[s:s + win].cpu().numpy(), orc.ecb(0, key, x[s:s + win].cpu().numpy(), nthreads=16)), s
+    aesgb.aes_ecb_crypt_cfg(1, dec, nr, y, y, n, c)
+    torch.cuda.synchronize()
+    assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("keybits", [128, 192, 256])
+@pytest.mark.parametrize("cfg", [(256, 8, 0), (256, 8, 5), (256, 1, 6), (256, 2, 6)])
+def test_1gib_register_and_128B_layouts_windows_and_roundtrip(orc, keybits, cfg):
+    """The placement study's additions at the size it times them (1 GiB): 128 B
+    per thread on the R4 and R2 tables, and the table in registers at 16 and
+    32 B per thread.  Encryption windows against the oracle; decryption in
+    place back to the input; encryption equal to the default configuration's
+    over the whole buffer."""
+    torch = torch_cuda()
+    nbytes = GIB
+    n = nbytes // 16
+    x = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    _fill_random(torch, x, 76 + keybits)
+    key = wl.random_key(keybits, 76).tobytes()
+    enc, dec, nr = aesgb.aes_expand_key(keybits, key)
+    c = aesgb.make_cfg(cfg[0], cfg[1], cfg[2], 0)
+    ref = torch.empty_like(x)
+    aesgb.aes_ecb_encrypt(enc, nr, x, ref, n)
+    y = torch.empty_like(x)
+    aesgb.aes_ecb_crypt_cfg(0, enc, nr, x, y, n, c)
+    torch.cuda.synchronize()
+    assert torch.equal(y, ref)
+    win = 64 * 1024
+    for s in _windows(nbytes, win, 77):
         assert np.array_equal(y[s:s + win].cpu().numpy(), orc.ecb(0, key, x[s:s + win].cpu().numpy(), nthreads=16)), s
     aesgb.aes_ecb_crypt_cfg(1, dec, nr, y, y, n, c)
     torch.cuda.synchronize()
